@@ -1,0 +1,198 @@
+/*
+ * nsdf.h - C ABI of the neural signed-distance collision library.
+ *
+ * The library answers collision queries against a body represented by a
+ * signed-distance network f: R^3 -> R (Eq. 1 of Bertiche, Madadi & Escalera,
+ * "Neural Implicit Surfaces for Efficient and Accurate Collisions in
+ * Physically Based Simulations").  For every query point p it evaluates
+ * f(p), the input gradient grad f(p) by back-propagation and the surface
+ * normal N = grad f / ||grad f|| (Eq. 2); a point collides when f(p) < eps
+ * (Sec. 3.2) and is then moved to its contact point p + (eps - f(p)) N
+ * (Eq. 3 with the naive solve of Sec. 3.2).  A body placed by a rigid
+ * transform T is queried at T^{-1} p and its normal rotated by T[:3,:3]
+ * (Sec. 4.2).
+ *
+ * Conventions shared by every entry point:
+ *  - Points are float4 records (x, y, z, w), 16-byte aligned, n of them
+ *    contiguous; w is ignored on input and copied through to projected
+ *    points.  Pointers that are not 16-byte aligned give NSDF_ERR_MISALIGNED.
+ *  - Buffers are owned by the caller.  Unless an entry point says otherwise
+ *    they are device pointers; the context owns only its weight copies,
+ *    its scratch and its error word.
+ *  - Calls are asynchronous on the given stream (NULL = legacy default
+ *    stream).  n == 0 is a successful no-op.  Nothing is thrown across the
+ *    ABI: every failure is a status code.
+ *  - Errors raised inside a kernel (a bounded wait that ran out) are
+ *    recorded in the context's error word and reported by
+ *    nsdf_sync_status().
+ *  - A context is used by one stream at a time; use one context per
+ *    concurrent stream.
+ */
+#ifndef NSDF_H
+#define NSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nsdf_ctx nsdf_ctx;
+
+/* Same object as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *nsdf_stream;
+
+typedef enum {
+  NSDF_OK = 0,
+  NSDF_ERR_INVALID_ARG = 1,  /* bad pointer, size, shape or index            */
+  NSDF_ERR_MISALIGNED = 2,   /* point / output pointer not 16-byte aligned   */
+  NSDF_ERR_NOT_LOADED = 3,   /* query before nsdf_load_weights for that net  */
+  NSDF_ERR_OOM = 4,          /* device allocation failed                     */
+  NSDF_ERR_CUDA = 5,         /* a CUDA runtime call failed                   */
+  NSDF_ERR_UNSUPPORTED = 6,  /* shape / precision this build has no kernel for */
+  NSDF_ERR_TIMEOUT = 7       /* a bounded wait inside a kernel ran out        */
+} nsdf_status;
+
+typedef enum {
+  NSDF_FP32 = 0,  /* FP32 CUDA-core arithmetic throughout                     */
+  NSDF_BF16 = 1   /* hidden-layer products on BF16 tensor cores, FP32 accumulate */
+} nsdf_precision;
+
+/*
+ * Network shape (Eq. 1): n_hidden softplus layers L0..L{n_hidden-1} of
+ * `width` units, then a linear output unit.  With skip_layer = s > 0,
+ * layer L{s-1} has width - in_dim units and L{s} reads [h_{s-1}, p] / sqrt(2).
+ * in_dim must be 3; beta > 0 is the softplus sharpness
+ * softplus(z) = log(1 + exp(beta z)) / beta.
+ */
+typedef struct {
+  int in_dim;
+  int width;
+  int n_hidden;
+  int skip_layer; /* -1: no skip */
+  float beta;
+} nsdf_arch;
+
+/* nsdf_query flag: return grad f instead of the unit normal. */
+#define NSDF_RAW_GRADIENT 1u
+
+/*
+ * Number of floats in a packed weight blob for `arch`: for each layer in
+ * order, W row-major [out x in] then b[out].  Returns 0 for an invalid arch.
+ */
+size_t nsdf_num_params(const nsdf_arch *arch);
+
+/*
+ * Create a context for n_nets networks of the same shape on the current
+ * device.  Synchronous.  Fails with NSDF_ERR_UNSUPPORTED when no kernel of
+ * this build handles (arch, prec): FP32 takes widths 32..512 in multiples of
+ * 32; BF16 takes width 512 (the body-scale network) and width 64.
+ */
+nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets,
+                        nsdf_ctx **out);
+
+/* Free the context and everything it owns.  Synchronises the device. */
+nsdf_status nsdf_destroy(nsdf_ctx *ctx);
+
+/*
+ * Load the packed FP32 blob `w` (n_floats == nsdf_num_params) of network
+ * `net`.  The library keeps its own converted copies (transposed, padded,
+ * BF16 where the precision asks); the caller keeps `w`.  w_is_device
+ * selects whether `w` is a device or a host pointer; with a host pointer the
+ * call returns after the copy has been taken.
+ */
+nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w,
+                              size_t n_floats, int w_is_device,
+                              nsdf_stream stream);
+
+/*
+ * Eq. 1-2 for network 0: out_n_sdf[i] = (N_x, N_y, N_z, f(p_i)) with N the
+ * unit normal (grad f if flags has NSDF_RAW_GRADIENT).  Where
+ * ||grad f|| < 1e-20 the normal is the zero vector.
+ */
+nsdf_status nsdf_query(nsdf_ctx *ctx, const float *pts, int64_t n,
+                       float *out_n_sdf, uint32_t flags, nsdf_stream stream);
+
+/*
+ * Collision test and naive solve (Sec. 3.2, Eq. 3, Sec. 4.2) for network 0.
+ *   T: NULL, or a 4x4 row-major rigid transform placing the body (host
+ *      memory, read during the call).
+ *   out_pts[i]   = p_i + (eps - f) N_world if f < eps, else p_i (w copied)
+ *   out_n_sdf[i] = (N_world, f)   (nullable)
+ *   out_hit[i]   = f < eps        (nullable, one byte per point)
+ * pts / out_pts / out_n_sdf / out_hit may all be device pointers, or all be
+ * host pointers: with host pointers the library streams chunks through its
+ * own device buffers (copies overlapped with compute) and returns once the
+ * results are in host memory.  out_pts may alias pts.
+ */
+nsdf_status nsdf_collide(nsdf_ctx *ctx, const float *pts, int64_t n, float eps,
+                         const float *T, float *out_pts, float *out_n_sdf,
+                         uint8_t *out_hit, nsdf_stream stream);
+
+/*
+ * Gradients of L = sum_i g_sdf[i] f(p_i) + g_grad[i] . grad f(p_i) for
+ * network 0 (training of Sec. 3.1; collision penalties).  g_grad is float4
+ * per point (w ignored) and nullable (= 0).  g_weights (nullable) receives
+ * dL/dtheta in blob layout (overwritten, FP32, nsdf_num_params floats);
+ * g_pts (nullable) receives dL/dp_i as float4 (w = 0).  Layer activations
+ * are recomputed, not stored.  FP32 arithmetic for either precision.
+ */
+nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n,
+                          const float *g_sdf, const float *g_grad,
+                          float *g_weights, float *g_pts, nsdf_stream stream);
+
+/*
+ * Many bodies in one launch: network k answers points
+ * pts[offsets[k] .. offsets[k] + counts[k]) for k < n_nets of the context.
+ * offsets and counts are DEVICE int64 arrays (so a captured CUDA graph can
+ * be replayed with new counts); max_total bounds offsets[k] + counts[k] and
+ * sizes the work list.  Outputs as nsdf_collide (no transform); out_n_sdf
+ * nullable.  Points outside every range are left untouched.
+ */
+nsdf_status nsdf_query_grouped(nsdf_ctx *ctx, const float *pts,
+                               const int64_t *offsets, const int64_t *counts,
+                               int64_t max_total, float eps, float *out_pts,
+                               float *out_n_sdf, nsdf_stream stream);
+
+/*
+ * Ground-truth signed distance to a watertight triangle mesh by brute force
+ * (the targets of Sec. 3.1): out_sdf[i] = +-min_t dist(p_i, triangle t),
+ * negative where the generalized winding number exceeds 1/2 (interior
+ * negative, Sec. 3.2).  verts: float [n_verts*3]; faces: int32 [n_faces*3],
+ * counter-clockwise seen from outside; pts float4; all device pointers.
+ * The winding number is accumulated in FP32 and recomputed in FP64 for
+ * points with |w - 1/2| < 0.25 or distance < 1e-3.
+ */
+nsdf_status nsdf_mesh_sdf(const float *verts, int64_t n_verts,
+                          const int32_t *faces, int64_t n_faces,
+                          const float *pts, int64_t n, float *out_sdf,
+                          nsdf_stream stream);
+
+/*
+ * One explicit Verlet step of a rectangular quad cloth (Sec. 4.1) on an
+ * nx-by-ny grid (float4 positions, row-major, row = z index): structural and
+ * shear springs with rest lengths from the grid spacings hx (along rows) and
+ * hz (between rows), unit mass, Hooke constant k_over_m, gravity (0, -g, 0):
+ *   x_new = 2 x - x_prev + dt^2 a(x).
+ * Writes x_new into x_prev's buffer (the caller swaps the two).  The
+ * collision solve is a separate nsdf_collide call on the result.
+ */
+nsdf_status nsdf_cloth_step(const float *x, float *x_prev_inout, int nx,
+                            int ny, float hx, float hz, float k_over_m,
+                            float g, float dt, nsdf_stream stream);
+
+/*
+ * Synchronise `stream`, then report (and clear) an error recorded by a
+ * kernel of this context: NSDF_ERR_TIMEOUT when a bounded wait ran out.
+ */
+nsdf_status nsdf_sync_status(nsdf_ctx *ctx, nsdf_stream stream);
+
+/* Static, human-readable name of a status code. */
+const char *nsdf_status_string(nsdf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSDF_H */

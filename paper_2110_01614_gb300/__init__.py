@@ -1,0 +1,186 @@
+"""Python binding of the nsdf C ABI (GB300-native neural-SDF collision queries).
+
+Functions carry the names of the C entry points in ``include/nsdf.h`` and
+only marshal arguments: tensors become raw pointers, the stream defaults to
+PyTorch's current stream, and a non-OK status raises ``NsdfError``.  All
+arithmetic runs in the CUDA kernels of ``libnsdf.so``; importing this
+package loads that library and fails loudly if it has not been built.
+
+Layouts (see the header for the full contract): points and results are
+float32 tensors of shape [n, 4]; weight blobs are float32 vectors in the
+packed layout of ``nsdf_num_params``.
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import (NSDF_BF16, NSDF_FP32, NSDF_RAW_GRADIENT, nsdf_arch)
+
+__all__ = [
+    "NsdfError", "NSDF_FP32", "NSDF_BF16", "NSDF_RAW_GRADIENT", "make_arch",
+    "nsdf_num_params", "nsdf_create", "nsdf_destroy", "nsdf_load_weights",
+    "nsdf_query", "nsdf_collide", "nsdf_backward", "nsdf_query_grouped",
+    "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status",
+    "nsdf_status_string", "NeuralSDF", "library",
+]
+
+
+def library():
+    """The loaded ctypes library (loads it on first use)."""
+    return _abi.load()
+
+
+class NsdfError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        msg = library().nsdf_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})")
+
+
+def _check(status, what):
+    if status != _abi.NSDF_OK:
+        raise NsdfError(status, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("nsdf needs contiguous tensors")
+        return t.data_ptr()
+    return int(t)
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def make_arch(width, n_hidden, skip_layer=-1, beta=100.0, in_dim=3):
+    return nsdf_arch(in_dim, width, n_hidden, skip_layer, beta)
+
+
+def _arch(a):
+    if isinstance(a, nsdf_arch):
+        return a
+    return nsdf_arch(a.in_dim, a.width, a.n_hidden, a.skip_layer, a.beta)
+
+
+def nsdf_status_string(status):
+    return library().nsdf_status_string(status).decode()
+
+
+def nsdf_num_params(arch):
+    return int(library().nsdf_num_params(ctypes.byref(_arch(arch))))
+
+
+def nsdf_create(arch, precision=NSDF_FP32, n_nets=1):
+    h = ctypes.c_void_p()
+    _check(library().nsdf_create(ctypes.byref(_arch(arch)), int(precision), int(n_nets),
+                                 ctypes.byref(h)), "nsdf_create")
+    return h.value
+
+
+def nsdf_destroy(ctx):
+    _check(library().nsdf_destroy(ctx), "nsdf_destroy")
+
+
+def nsdf_load_weights(ctx, net, w, stream=None):
+    if w.dtype != torch.float32:
+        raise ValueError("weight blob must be float32")
+    _check(library().nsdf_load_weights(ctx, int(net), _ptr(w), w.numel(), int(w.is_cuda),
+                                       _stream(stream)), "nsdf_load_weights")
+
+
+def nsdf_query(ctx, pts, out_n_sdf, flags=0, stream=None):
+    _check(library().nsdf_query(ctx, _ptr(pts), pts.shape[0], _ptr(out_n_sdf), int(flags),
+                                _stream(stream)), "nsdf_query")
+
+
+def _transform(T):
+    if T is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float32).reshape(16))
+    return (ctypes.c_float * 16)(*a.tolist())
+
+
+def nsdf_collide(ctx, pts, eps, out_pts, out_n_sdf=None, out_hit=None, T=None, stream=None):
+    Tc = _transform(T)
+    _check(library().nsdf_collide(ctx, _ptr(pts), pts.shape[0], float(eps),
+                                  ctypes.cast(Tc, ctypes.c_void_p) if Tc is not None else None,
+                                  _ptr(out_pts), _ptr(out_n_sdf), _ptr(out_hit),
+                                  _stream(stream)), "nsdf_collide")
+
+
+def nsdf_backward(ctx, pts, g_sdf, g_grad=None, g_weights=None, g_pts=None, stream=None):
+    _check(library().nsdf_backward(ctx, _ptr(pts), pts.shape[0], _ptr(g_sdf), _ptr(g_grad),
+                                   _ptr(g_weights), _ptr(g_pts), _stream(stream)),
+           "nsdf_backward")
+
+
+def nsdf_query_grouped(ctx, pts, offsets, counts, max_total, eps, out_pts, out_n_sdf=None,
+                       stream=None):
+    _check(library().nsdf_query_grouped(ctx, _ptr(pts), _ptr(offsets), _ptr(counts),
+                                        int(max_total), float(eps), _ptr(out_pts),
+                                        _ptr(out_n_sdf), _stream(stream)), "nsdf_query_grouped")
+
+
+def nsdf_mesh_sdf(verts, faces, pts, out_sdf, stream=None):
+    _check(library().nsdf_mesh_sdf(_ptr(verts), verts.shape[0], _ptr(faces), faces.shape[0],
+                                   _ptr(pts), pts.shape[0], _ptr(out_sdf), _stream(stream)),
+           "nsdf_mesh_sdf")
+
+
+def nsdf_cloth_step(x, x_prev, nx, ny, hx, hz, k_over_m, g, dt, stream=None):
+    _check(library().nsdf_cloth_step(_ptr(x), _ptr(x_prev), int(nx), int(ny), float(hx),
+                                     float(hz), float(k_over_m), float(g), float(dt),
+                                     _stream(stream)), "nsdf_cloth_step")
+
+
+def nsdf_sync_status(ctx, stream=None):
+    _check(library().nsdf_sync_status(ctx, _stream(stream)), "nsdf_sync_status")
+
+
+class NeuralSDF:
+    """Owns one nsdf context (n_nets networks of one shape) on the current GPU."""
+
+    def __init__(self, arch, precision=NSDF_FP32, n_nets=1):
+        self.arch = _arch(arch)
+        self.precision = precision
+        self.n_nets = n_nets
+        self.ctx = nsdf_create(self.arch, precision, n_nets)
+
+    def load(self, blob, net=0, stream=None):
+        w = torch.as_tensor(blob, dtype=torch.float32)
+        if not w.is_cuda:
+            w = w.contiguous()
+        nsdf_load_weights(self.ctx, net, w, stream)
+        return self
+
+    def query(self, pts, raw_gradient=False, out=None, stream=None):
+        out = torch.empty_like(pts) if out is None else out
+        nsdf_query(self.ctx, pts, out, NSDF_RAW_GRADIENT if raw_gradient else 0, stream)
+        return out
+
+    def collide(self, pts, eps, T=None, out_pts=None, out_n_sdf=None, out_hit=None, stream=None):
+        out_pts = torch.empty_like(pts) if out_pts is None else out_pts
+        nsdf_collide(self.ctx, pts, eps, out_pts, out_n_sdf, out_hit, T, stream)
+        return out_pts
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            nsdf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

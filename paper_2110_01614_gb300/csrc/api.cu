@@ -1,0 +1,509 @@
+// Host runtime and C ABI of the nsdf library (declared in include/nsdf.h).
+//
+// Owns contexts, converts weight blobs into the kernels' device layouts,
+// validates arguments, sizes scratch and launches the kernels on the
+// caller's stream.  Host-memory collision calls are streamed through device
+// staging buffers in chunks on two internal streams so that copies overlap
+// compute.
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nsdf_internal.h"
+
+using namespace nsdf;
+
+namespace {
+
+constexpr int kMaxLayers = 64;
+
+bool arch_valid(const nsdf_arch *a) {
+  if (!a) return false;
+  if (a->in_dim != 3 || a->width < 4 || a->n_hidden < 1 || a->n_hidden > kMaxLayers - 1) return false;
+  if (!(a->beta > 0.0f) || !std::isfinite(a->beta)) return false;
+  if (a->skip_layer != -1 && (a->skip_layer < 1 || a->skip_layer >= a->n_hidden)) return false;
+  return true;
+}
+
+int layer_out(const nsdf_arch &a, int l) {
+  if (l == a.n_hidden) return 1;
+  if (a.skip_layer > 0 && l == a.skip_layer - 1) return a.width - a.in_dim;
+  return a.width;
+}
+int layer_in(const nsdf_arch &a, int l) { return l == 0 ? a.in_dim : a.width; }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// 0: device (or managed), 1: host (pinned or pageable), -1: error
+int pointer_kind(const void *p) {
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) return 0;
+  return 1;
+}
+
+bool invert4x4(const double *m, double *inv) {
+  double a[4][8];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 8; ++c) a[r][c] = c < 4 ? m[r * 4 + c] : (c - 4 == r ? 1.0 : 0.0);
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (std::fabs(a[r][c]) > std::fabs(a[piv][c])) piv = r;
+    if (std::fabs(a[piv][c]) < 1e-300) return false;
+    if (piv != c)
+      for (int k = 0; k < 8; ++k) std::swap(a[c][k], a[piv][k]);
+    const double d = a[c][c];
+    for (int k = 0; k < 8; ++k) a[c][k] /= d;
+    for (int r = 0; r < 4; ++r)
+      if (r != c) {
+        const double f = a[r][c];
+        for (int k = 0; k < 8; ++k) a[r][k] -= f * a[c][k];
+      }
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) inv[r * 4 + c] = a[r][c + 4];
+  return true;
+}
+
+struct PackPlan {
+  int width, n_hidden, skip;
+  int64_t woff[kMaxLayers];
+  int64_t boff[kMaxLayers];
+  int out[kMaxLayers];
+};
+
+// Converts the packed FP32 blob into every device layout the kernels read.
+__global__ void pack_weights_kernel(const float *__restrict__ blob, PackPlan plan, NetDevice net) {
+  const int W = plan.width, L = plan.n_hidden;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // L0 weights and all hidden biases, output layer
+  for (int64_t t = t0; t < (int64_t)W * 3; t += stride) {
+    const int n = (int)(t / 3), k = (int)(t % 3);
+    net.w0[t] = n < plan.out[0] ? blob[plan.woff[0] + (int64_t)n * 3 + k] : 0.0f;
+  }
+  for (int64_t t = t0; t < (int64_t)L * W; t += stride) {
+    const int l = (int)(t / W), n = (int)(t % W);
+    net.bias[t] = n < plan.out[l] ? blob[plan.boff[l] + n] : 0.0f;
+  }
+  for (int64_t t = t0; t < W; t += stride) net.wout[t] = blob[plan.woff[L] + t];
+  if (t0 == 0) net.bout[0] = blob[plan.boff[L]];
+  // hidden layers l = 1 .. L-1, padded to W x W
+  const int64_t per = (int64_t)W * W;
+  for (int64_t t = t0; t < (int64_t)(L - 1) * per; t += stride) {
+    const int l = 1 + (int)(t / per);
+    const int64_t e = t % per;
+    const int r = (int)(e / W), c = (int)(e % W);
+    const float *Wl = blob + plan.woff[l];          // [out_l x W] row-major
+    // row-major [r][c] element of each layout
+    const float w_rc = r < plan.out[l] ? Wl[(int64_t)r * W + c] : 0.0f;   // W_l[r][c]
+    const float w_cr = c < plan.out[l] ? Wl[(int64_t)c * W + r] : 0.0f;   // W_l[c][r]
+    const int64_t o = (int64_t)(l - 1) * per + e;
+    net.fwd_t[o] = w_cr;   // [k=r][n=c] = W_l[n][k]
+    net.bwd[o] = w_rc;     // [n=r][k=c] = W_l[n][k]
+    if (net.fwd16) {
+      net.fwd16[o] = __float2bfloat16_rn(w_rc);   // [n=r][k=c]
+      net.bwd16[o] = __float2bfloat16_rn(w_cr);   // [k=r][n=c]
+    }
+  }
+}
+
+cudaError_t last_err() { return cudaGetLastError(); }
+
+}  // namespace
+
+struct nsdf_ctx {
+  nsdf_arch arch{};
+  nsdf_precision prec = NSDF_FP32;
+  int n_nets = 0;
+  int device = 0;
+  int num_sms = 0;
+  std::vector<NetDevice> nets;
+  std::vector<void *> allocations;
+  float *scratch = nullptr;     // per-CTA slope slabs of the query kernels
+  size_t scratch_bytes = 0;
+  int *d_err = nullptr;         // device error word
+  // host-buffer pipeline
+  cudaStream_t pipe[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr, ev_done[2] = {nullptr, nullptr};
+  float *stage = nullptr;       // 2 x chunk x (4 + 4 + 4 floats) + 2 x chunk bytes
+  float *pipe_scratch[2] = {nullptr, nullptr};
+  size_t pipe_scratch_bytes = 0;
+  int64_t chunk = 0;
+};
+
+namespace {
+
+nsdf_status map_err(cudaError_t e) {
+  if (e == cudaSuccess) return NSDF_OK;
+  if (e == cudaErrorMemoryAllocation) return NSDF_ERR_OOM;
+  return NSDF_ERR_CUDA;
+}
+
+template <typename T>
+nsdf_status ctx_alloc(nsdf_ctx *ctx, T **p, size_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return NSDF_ERR_OOM;
+  }
+  ctx->allocations.push_back(q);
+  *p = static_cast<T *>(q);
+  return NSDF_OK;
+}
+
+bool use_bf16(const nsdf_ctx *ctx) { return ctx->prec == NSDF_BF16; }
+
+int query_grid(const nsdf_ctx *ctx, int64_t n) {
+  if (use_bf16(ctx)) return query_bf16_grid(ctx->arch.width, n, ctx->num_sms);
+  return query_fp32_grid(ctx->arch.width, n, ctx->num_sms);
+}
+
+size_t query_scratch(const nsdf_ctx *ctx, int grid) {
+  if (use_bf16(ctx)) return query_bf16_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
+  return query_fp32_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
+}
+
+nsdf_status ensure_scratch(nsdf_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->scratch_bytes) return NSDF_OK;
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  ctx->scratch = nullptr;
+  ctx->scratch_bytes = 0;
+  void *q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return NSDF_ERR_OOM;
+  }
+  ctx->scratch = static_cast<float *>(q);
+  ctx->scratch_bytes = bytes;
+  return NSDF_OK;
+}
+
+void fill_net(const nsdf_ctx *ctx, int net, QueryParams &p) {
+  const NetDevice &d = ctx->nets[net];
+  p.w0 = d.w0; p.bias = d.bias; p.fwd_t = d.fwd_t; p.bwd = d.bwd; p.wout = d.wout; p.bout = d.bout;
+  p.fwd16 = d.fwd16; p.bwd16 = d.bwd16;
+  p.width = ctx->arch.width;
+  p.n_hidden = ctx->arch.n_hidden;
+  p.skip = ctx->arch.skip_layer;
+  p.beta = ctx->arch.beta;
+  p.err = ctx->d_err;
+}
+
+cudaError_t launch_query(const nsdf_ctx *ctx, const QueryParams &p, cudaStream_t s) {
+  if (use_bf16(ctx)) return launch_query_bf16(p, ctx->num_sms, s);
+  return launch_query_fp32(p, ctx->num_sms, s);
+}
+
+nsdf_status set_transform(const float *T, QueryParams &p) {
+  p.has_T = 0;
+  if (!T) return NSDF_OK;
+  double m[16], inv[16];
+  for (int i = 0; i < 16; ++i) m[i] = T[i];
+  if (!invert4x4(m, inv)) return NSDF_ERR_INVALID_ARG;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 4; ++c) p.Ti[r * 4 + c] = (float)inv[r * 4 + c];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) p.R[r * 3 + c] = T[r * 4 + c];
+  p.has_T = 1;
+  return NSDF_OK;
+}
+
+nsdf_status ensure_pipeline(nsdf_ctx *ctx) {
+  if (ctx->stage) return NSDF_OK;
+  const int64_t chunk = 1 << 18;
+  cudaError_t e;
+  for (int i = 0; i < 2; ++i) {
+    e = cudaStreamCreateWithFlags(&ctx->pipe[i], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return map_err(e);
+    e = cudaEventCreateWithFlags(&ctx->ev_done[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return map_err(e);
+  }
+  e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+  if (e != cudaSuccess) return map_err(e);
+  const size_t per = (size_t)chunk * (3 * 16 + 1);
+  void *q = nullptr;
+  if (cudaMalloc(&q, 2 * per + 64) != cudaSuccess) {
+    cudaGetLastError();
+    return NSDF_ERR_OOM;
+  }
+  ctx->stage = static_cast<float *>(q);
+  const int grid = query_grid(ctx, chunk);
+  const size_t sb = query_scratch(ctx, grid);
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&q, sb) != cudaSuccess) {
+      cudaGetLastError();
+      return NSDF_ERR_OOM;
+    }
+    ctx->pipe_scratch[i] = static_cast<float *>(q);
+  }
+  ctx->pipe_scratch_bytes = sb;
+  ctx->chunk = chunk;
+  return NSDF_OK;
+}
+
+// Collision solve on host buffers: chunks alternate between two streams;
+// each chunk is copied in, solved and copied out on its stream.
+nsdf_status collide_host(nsdf_ctx *ctx, QueryParams base, const float *pts, int64_t n,
+                         float *out_pts, float *out_n_sdf, uint8_t *out_hit, cudaStream_t s) {
+  nsdf_status st = ensure_pipeline(ctx);
+  if (st != NSDF_OK) return st;
+  const int64_t chunk = ctx->chunk;
+  cudaError_t e = cudaEventRecord(ctx->ev_start, s);
+  if (e != cudaSuccess) return map_err(e);
+  for (int i = 0; i < 2; ++i) cudaStreamWaitEvent(ctx->pipe[i], ctx->ev_start, 0);
+  const size_t per = (size_t)chunk * (3 * 16 + 1);
+  for (int64_t c0 = 0, k = 0; c0 < n; c0 += chunk, ++k) {
+    const int b = (int)(k & 1);
+    cudaStream_t ps = ctx->pipe[b];
+    char *base_b = reinterpret_cast<char *>(ctx->stage) + b * per;
+    float4 *d_in = reinterpret_cast<float4 *>(base_b);
+    float4 *d_out = d_in + chunk;
+    float4 *d_nsdf = d_out + chunk;
+    uint8_t *d_hit = reinterpret_cast<uint8_t *>(d_nsdf + chunk);
+    const int64_t m = (n - c0 < chunk) ? n - c0 : chunk;
+    e = cudaMemcpyAsync(d_in, pts + 4 * c0, (size_t)m * 16, cudaMemcpyHostToDevice, ps);
+    if (e != cudaSuccess) return map_err(e);
+    QueryParams p = base;
+    p.pts = d_in;
+    p.n = m;
+    p.out_pts = d_out;
+    p.out_n_sdf = out_n_sdf ? d_nsdf : nullptr;
+    p.out_hit = out_hit ? d_hit : nullptr;
+    p.scratch = ctx->pipe_scratch[b];
+    e = launch_query(ctx, p, ps);
+    if (e != cudaSuccess) return map_err(e);
+    if (out_pts) {
+      e = cudaMemcpyAsync(out_pts + 4 * c0, d_out, (size_t)m * 16, cudaMemcpyDeviceToHost, ps);
+      if (e != cudaSuccess) return map_err(e);
+    }
+    if (out_n_sdf) {
+      e = cudaMemcpyAsync(out_n_sdf + 4 * c0, d_nsdf, (size_t)m * 16, cudaMemcpyDeviceToHost, ps);
+      if (e != cudaSuccess) return map_err(e);
+    }
+    if (out_hit) {
+      e = cudaMemcpyAsync(out_hit + c0, d_hit, (size_t)m, cudaMemcpyDeviceToHost, ps);
+      if (e != cudaSuccess) return map_err(e);
+    }
+  }
+  for (int i = 0; i < 2; ++i) {
+    cudaEventRecord(ctx->ev_done[i], ctx->pipe[i]);
+    cudaStreamWaitEvent(s, ctx->ev_done[i], 0);
+  }
+  e = cudaStreamSynchronize(s);
+  return map_err(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t nsdf_num_params(const nsdf_arch *arch) {
+  if (!arch_valid(arch)) return 0;
+  size_t total = 0;
+  for (int l = 0; l <= arch->n_hidden; ++l)
+    total += (size_t)layer_out(*arch, l) * layer_in(*arch, l) + layer_out(*arch, l);
+  return total;
+}
+
+const char *nsdf_status_string(nsdf_status s) {
+  switch (s) {
+    case NSDF_OK: return "ok";
+    case NSDF_ERR_INVALID_ARG: return "invalid argument";
+    case NSDF_ERR_MISALIGNED: return "pointer not 16-byte aligned";
+    case NSDF_ERR_NOT_LOADED: return "weights not loaded";
+    case NSDF_ERR_OOM: return "device allocation failed";
+    case NSDF_ERR_CUDA: return "CUDA runtime error";
+    case NSDF_ERR_UNSUPPORTED: return "unsupported shape or precision";
+    case NSDF_ERR_TIMEOUT: return "bounded wait in a kernel ran out";
+  }
+  return "unknown status";
+}
+
+nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, nsdf_ctx **out) {
+  if (!out) return NSDF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!arch_valid(arch) || n_nets < 1 || n_nets > 4096) return NSDF_ERR_INVALID_ARG;
+  if (prec != NSDF_FP32 && prec != NSDF_BF16) return NSDF_ERR_INVALID_ARG;
+  if (prec == NSDF_FP32 && !query_fp32_supported(arch->width)) return NSDF_ERR_UNSUPPORTED;
+  if (prec == NSDF_BF16 && !query_bf16_supported(arch->width, arch->n_hidden, arch->skip_layer))
+    return NSDF_ERR_UNSUPPORTED;
+  nsdf_ctx *ctx = new (std::nothrow) nsdf_ctx;
+  if (!ctx) return NSDF_ERR_OOM;
+  ctx->arch = *arch;
+  ctx->prec = prec;
+  ctx->n_nets = n_nets;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return map_err(e);
+  }
+  const int W = arch->width, L = arch->n_hidden;
+  ctx->nets.resize(n_nets);
+  nsdf_status st = NSDF_OK;
+  for (int k = 0; k < n_nets && st == NSDF_OK; ++k) {
+    NetDevice &d = ctx->nets[k];
+    const size_t hid = (size_t)(L > 1 ? L - 1 : 1) * W * W;
+    if (st == NSDF_OK) st = ctx_alloc(ctx, &d.w0, (size_t)W * 3);
+    if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bias, (size_t)L * W);
+    if (st == NSDF_OK) st = ctx_alloc(ctx, &d.fwd_t, hid);
+    if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd, hid);
+    if (st == NSDF_OK) st = ctx_alloc(ctx, &d.wout, (size_t)W);
+    if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bout, 4);
+    if (st == NSDF_OK && prec == NSDF_BF16) {
+      st = ctx_alloc(ctx, &d.fwd16, hid);
+      if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd16, hid);
+    }
+  }
+  if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_err, 4);
+  if (st == NSDF_OK) st = map_err(cudaMemset(ctx->d_err, 0, sizeof(int)));
+  if (st != NSDF_OK) {
+    nsdf_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return NSDF_OK;
+}
+
+nsdf_status nsdf_destroy(nsdf_ctx *ctx) {
+  if (!ctx) return NSDF_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  for (void *p : ctx->allocations) cudaFree(p);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->stage) cudaFree(ctx->stage);
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->pipe_scratch[i]) cudaFree(ctx->pipe_scratch[i]);
+    if (ctx->pipe[i]) cudaStreamDestroy(ctx->pipe[i]);
+    if (ctx->ev_done[i]) cudaEventDestroy(ctx->ev_done[i]);
+  }
+  if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+  delete ctx;
+  return NSDF_OK;
+}
+
+nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w, size_t n_floats,
+                              int w_is_device, nsdf_stream stream) {
+  if (!ctx || !w || net < 0 || net >= ctx->n_nets) return NSDF_ERR_INVALID_ARG;
+  if (n_floats != nsdf_num_params(&ctx->arch)) return NSDF_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const float *src = w;
+  float *tmp = nullptr;
+  if (!w_is_device) {
+    if (cudaMalloc(&tmp, n_floats * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return NSDF_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpyAsync(tmp, w, n_floats * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return map_err(e);
+    }
+    src = tmp;
+  }
+  PackPlan plan{};
+  const nsdf_arch &a = ctx->arch;
+  plan.width = a.width;
+  plan.n_hidden = a.n_hidden;
+  plan.skip = a.skip_layer;
+  int64_t off = 0;
+  for (int l = 0; l <= a.n_hidden; ++l) {
+    plan.out[l] = layer_out(a, l);
+    plan.woff[l] = off;
+    off += (int64_t)layer_out(a, l) * layer_in(a, l);
+    plan.boff[l] = off;
+    off += layer_out(a, l);
+  }
+  pack_weights_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(src, plan, ctx->nets[net]);
+  cudaError_t e = last_err();
+  if (tmp) {
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) return map_err(e);
+  ctx->nets[net].loaded = true;
+  return NSDF_OK;
+}
+
+nsdf_status nsdf_query(nsdf_ctx *ctx, const float *pts, int64_t n, float *out_n_sdf,
+                       uint32_t flags, nsdf_stream stream) {
+  if (!ctx || n < 0) return NSDF_ERR_INVALID_ARG;
+  if (n == 0) return NSDF_OK;
+  if (!pts || !out_n_sdf) return NSDF_ERR_INVALID_ARG;
+  if (!aligned16(pts) || !aligned16(out_n_sdf)) return NSDF_ERR_MISALIGNED;
+  if (!ctx->nets[0].loaded) return NSDF_ERR_NOT_LOADED;
+  if (pointer_kind(pts) != 0 || pointer_kind(out_n_sdf) != 0) return NSDF_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  QueryParams p{};
+  fill_net(ctx, 0, p);
+  p.pts = reinterpret_cast<const float4 *>(pts);
+  p.n = n;
+  p.out_n_sdf = reinterpret_cast<float4 *>(out_n_sdf);
+  p.collide = 0;
+  p.raw_gradient = (flags & NSDF_RAW_GRADIENT) ? 1 : 0;
+  const int grid = query_grid(ctx, n);
+  nsdf_status st = ensure_scratch(ctx, query_scratch(ctx, grid));
+  if (st != NSDF_OK) return st;
+  p.scratch = ctx->scratch;
+  return map_err(launch_query(ctx, p, s));
+}
+
+nsdf_status nsdf_collide(nsdf_ctx *ctx, const float *pts, int64_t n, float eps, const float *T,
+                         float *out_pts, float *out_n_sdf, uint8_t *out_hit, nsdf_stream stream) {
+  if (!ctx || n < 0 || !std::isfinite(eps)) return NSDF_ERR_INVALID_ARG;
+  if (n == 0) return NSDF_OK;
+  if (!pts || !out_pts) return NSDF_ERR_INVALID_ARG;
+  if (!aligned16(pts) || !aligned16(out_pts) || (out_n_sdf && !aligned16(out_n_sdf)))
+    return NSDF_ERR_MISALIGNED;
+  if (!ctx->nets[0].loaded) return NSDF_ERR_NOT_LOADED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  QueryParams p{};
+  fill_net(ctx, 0, p);
+  p.collide = 1;
+  p.eps = eps;
+  nsdf_status st = set_transform(T, p);
+  if (st != NSDF_OK) return st;
+  const int kin = pointer_kind(pts);
+  const int kout = pointer_kind(out_pts);
+  const int kn = out_n_sdf ? pointer_kind(out_n_sdf) : kin;
+  const int kh = out_hit ? pointer_kind(out_hit) : kin;
+  if (kin != kout || kin != kn || kin != kh) return NSDF_ERR_INVALID_ARG;
+  if (kin == 1) return collide_host(ctx, p, pts, n, out_pts, out_n_sdf, out_hit, s);
+  p.pts = reinterpret_cast<const float4 *>(pts);
+  p.n = n;
+  p.out_pts = reinterpret_cast<float4 *>(out_pts);
+  p.out_n_sdf = reinterpret_cast<float4 *>(out_n_sdf);
+  p.out_hit = out_hit;
+  const int grid = query_grid(ctx, n);
+  st = ensure_scratch(ctx, query_scratch(ctx, grid));
+  if (st != NSDF_OK) return st;
+  p.scratch = ctx->scratch;
+  return map_err(launch_query(ctx, p, s));
+}
+
+nsdf_status nsdf_sync_status(nsdf_ctx *ctx, nsdf_stream stream) {
+  if (!ctx) return NSDF_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return map_err(e);
+  int h = 0;
+  e = cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return map_err(e);
+  if (h != kDevOk) {
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    return NSDF_ERR_TIMEOUT;
+  }
+  return NSDF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Internal declarations shared by the host runtime and the kernels of the
+// nsdf library.  Nothing here is part of the public ABI (include/nsdf.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "nsdf.h"
+
+namespace nsdf {
+
+// Kernel-side error codes written into a context's device error word.
+enum DeviceError : int {
+  kDevOk = 0,
+  kDevTimeout = 1,   // a bounded mbarrier wait gave up
+};
+
+// Device copies of one network, in the layouts the kernels read.
+// Hidden layers l = 1 .. n_hidden-1 are padded to width x width (a layer
+// with fewer outputs gets zero rows and zero biases).
+struct NetDevice {
+  // FP32 forms
+  float *w0 = nullptr;     // [width][3]   L0 weights, row n = (W0[n][0..2])
+  float *bias = nullptr;   // [n_hidden][width]
+  float *fwd_t = nullptr;  // [n_hidden-1][width(k)][width(n)] = W_l[n][k]
+  float *bwd = nullptr;    // [n_hidden-1][width(n)][width(k)] = W_l[n][k]
+  float *wout = nullptr;   // [width]      output weights (zero padded)
+  float *bout = nullptr;   // [1]
+  // BF16 forms (tensor-core B operands, K-major)
+  __nv_bfloat16 *fwd16 = nullptr;  // [n_hidden-1][width(n)][width(k)] = W_l
+  __nv_bfloat16 *bwd16 = nullptr;  // [n_hidden-1][width(k)][width(n)] = W_l^T
+  bool loaded = false;
+};
+
+// Everything one fused query launch needs (passed by value).
+struct QueryParams {
+  const float4 *pts;
+  int64_t n;
+  float4 *out_n_sdf;   // nullable
+  float4 *out_pts;     // nullable (query mode)
+  uint8_t *out_hit;    // nullable
+  float eps;
+  int collide;         // 1: collision solve, 0: plain query
+  int raw_gradient;    // query mode: output grad f instead of N
+  int has_T;
+  float Ti[12];        // T^{-1}, rows 0..2 of the 4x4 (row-major)
+  float R[9];          // T[:3,:3]
+  // network
+  const float *w0, *bias, *fwd_t, *bwd, *wout, *bout;
+  const __nv_bfloat16 *fwd16, *bwd16;
+  int width, n_hidden, skip;
+  float beta;
+  // per-CTA scratch and the context's error word
+  float *scratch;
+  int *err;
+};
+
+// Launchers (return a cudaError_t from the launch).
+cudaError_t launch_query_fp32(const QueryParams &p, int num_sms, cudaStream_t s);
+size_t query_fp32_scratch_bytes(int width, int n_hidden, int grid);
+int query_fp32_grid(int width, int64_t n, int num_sms);
+bool query_fp32_supported(int width);
+
+bool query_bf16_supported(int width, int n_hidden, int skip);
+cudaError_t launch_query_bf16(const QueryParams &p, int num_sms, cudaStream_t s);
+size_t query_bf16_scratch_bytes(int width, int n_hidden, int grid);
+int query_bf16_grid(int width, int64_t n, int num_sms);
+
+}  // namespace nsdf

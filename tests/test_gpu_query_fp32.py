@@ -1,0 +1,208 @@
+"""GPU parity of the FP32 CUDA-core fused query against the FP64 oracle.
+
+Tolerances (FP32 form): |delta sdf| <= 1e-5 and normal angle <= 1e-4 rad,
+element by element; collision decisions must agree wherever the oracle's
+f is farther than 1e-5 from eps.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import mlp
+from parity import normal_angle
+
+pytestmark = pytest.mark.gpu
+
+TINY = synth.Arch(3, 64, 3, -1, 100.0)
+BODY = synth.Arch(3, 512, 8, 4, 100.0)
+SDF_TOL, ANG_TOL = 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module")
+def nsdf(nsdf_lib):
+    import paper_2110_01614_gb300 as m
+    return m
+
+
+def run_query(nsdf, arch, blob, pts, raw=False):
+    sdf = nsdf.NeuralSDF(arch, nsdf.NSDF_FP32).load(blob)
+    d = torch.from_numpy(pts).cuda()
+    out = sdf.query(d, raw_gradient=raw)
+    torch.cuda.synchronize()
+    sdf.close()
+    return out.cpu().numpy()
+
+
+def check_query(out, f, g):
+    ok = np.linalg.norm(g, axis=1) > 1e-6
+    assert np.abs(out[:, 3] - f).max() <= SDF_TOL
+    assert normal_angle(g[ok], out[ok, :3]).max() <= ANG_TOL
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 1000, 4096])
+def test_tiny_network_query(nsdf, n):
+    blob = synth.geometric_init(TINY, 0)
+    pts = synth.uniform_cube_points(n, 1)
+    out = run_query(nsdf, TINY, blob, pts)
+    f, g = mlp.query(blob, TINY, pts, raw_gradient=True)
+    check_query(out, f, g)
+    np.testing.assert_allclose(np.linalg.norm(out[:, :3], axis=1), 1.0, atol=1e-6)
+
+
+def test_raw_gradient_flag(nsdf):
+    blob = synth.geometric_init(TINY, 0)
+    pts = synth.uniform_cube_points(777, 2)
+    out = run_query(nsdf, TINY, blob, pts, raw=True)
+    f, g = mlp.query(blob, TINY, pts, raw_gradient=True)
+    np.testing.assert_allclose(out[:, :3], g, atol=2e-5, rtol=1e-4)
+
+
+@pytest.mark.parametrize("n", [4096 + 17])
+def test_body_scale_network_query(nsdf, n):
+    blob = synth.geometric_init(BODY, 0)
+    pts = synth.body_scale_points(n, 1)
+    out = run_query(nsdf, BODY, blob, pts)
+    f, g = mlp.query(blob, BODY, pts, raw_gradient=True)
+    check_query(out, f, g)
+
+
+@pytest.mark.parametrize("width,n_hidden,skip", [(32, 2, -1), (128, 4, 2), (256, 3, 1),
+                                                 (64, 1, -1)])
+def test_other_shapes(nsdf, width, n_hidden, skip):
+    arch = synth.Arch(3, width, n_hidden, skip, 100.0)
+    blob = synth.geometric_init(arch, 3)
+    pts = synth.body_scale_points(999, 4)
+    out = run_query(nsdf, arch, blob, pts)
+    f, g = mlp.query(blob, arch, pts, raw_gradient=True)
+    check_query(out, f, g)
+
+
+def rigid(seed):
+    s = synth.Stream(seed, tag=5)
+    q = s.normal(4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                  [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                  [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = s.uniform(3, -0.3, 0.3)
+    return T
+
+
+def check_collide(f_ref, N_ref, hit_ref, x_ref, eps, out_pts, out_ns, out_hit, pts):
+    assert np.abs(out_ns[:, 3] - f_ref).max() <= SDF_TOL
+    ok = np.linalg.norm(N_ref, axis=1) > 0
+    assert normal_angle(N_ref[ok], out_ns[ok, :3]).max() <= ANG_TOL
+    clear = np.abs(f_ref - eps) > SDF_TOL
+    np.testing.assert_array_equal(out_hit[clear].astype(bool), hit_ref[clear])
+    # projected points: p + (eps - f) N, error bounded by the sdf and angle errors
+    tol = SDF_TOL + ANG_TOL * np.abs(eps - f_ref) + 1e-6
+    same = clear
+    err = np.linalg.norm(out_pts[same, :3] - x_ref[same], axis=1)
+    assert np.all(err <= tol[same])
+    np.testing.assert_array_equal(out_pts[:, 3], pts[:, 3])
+
+
+@pytest.mark.parametrize("with_T", [False, True])
+def test_collide_body_scale(nsdf, with_T):
+    blob = synth.geometric_init(BODY, 0)
+    pts = synth.body_scale_points(3000, 5)
+    pts[:, 3] = np.arange(3000, dtype=np.float32)     # w rides along unchanged
+    T = rigid(2) if with_T else None
+    eps = 0.002
+    f, N, hit, x = mlp.collide(blob, BODY, pts, eps, T)
+    sdf = nsdf.NeuralSDF(BODY, nsdf.NSDF_FP32).load(blob)
+    d = torch.from_numpy(pts).cuda()
+    out_pts = torch.empty_like(d)
+    out_ns = torch.empty_like(d)
+    out_hit = torch.empty(3000, dtype=torch.uint8, device="cuda")
+    sdf.collide(d, eps, T=T, out_pts=out_pts, out_n_sdf=out_ns, out_hit=out_hit)
+    torch.cuda.synchronize()
+    sdf.close()
+    assert 0.05 < hit.mean() < 0.95
+    check_collide(f, N, hit, x, eps, out_pts.cpu().numpy(), out_ns.cpu().numpy(),
+                  out_hit.cpu().numpy(), pts)
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_collide_host_buffers_match_device_path(nsdf, pinned):
+    blob = synth.geometric_init(TINY, 0)
+    n = (1 << 18) + (1 << 17) + 5          # spans two pipeline chunks and a ragged one
+    pts = torch.from_numpy(synth.uniform_cube_points(n, 6))
+    if pinned:
+        pts = pts.pin_memory()
+    sdf = nsdf.NeuralSDF(TINY, nsdf.NSDF_FP32).load(blob)
+    host_out = torch.empty_like(pts)
+    host_ns = torch.empty_like(pts)
+    host_hit = torch.empty(n, dtype=torch.uint8)
+    if pinned:
+        host_out, host_ns, host_hit = host_out.pin_memory(), host_ns.pin_memory(), host_hit.pin_memory()
+    nsdf.nsdf_collide(sdf.ctx, pts, 0.002, host_out, host_ns, host_hit)
+    d = pts.cuda()
+    dev_out = torch.empty_like(d)
+    dev_ns = torch.empty_like(d)
+    dev_hit = torch.empty(n, dtype=torch.uint8, device="cuda")
+    nsdf.nsdf_collide(sdf.ctx, d, 0.002, dev_out, dev_ns, dev_hit)
+    torch.cuda.synchronize()
+    sdf.close()
+    assert torch.equal(host_out, dev_out.cpu())
+    assert torch.equal(host_ns, dev_ns.cpu())
+    assert torch.equal(host_hit, dev_hit.cpu())
+
+
+def test_edge_cases(nsdf):
+    blob = synth.geometric_init(TINY, 0)
+    sdf = nsdf.NeuralSDF(TINY, nsdf.NSDF_FP32)
+    d = torch.zeros(8, 4, device="cuda")
+    with pytest.raises(nsdf.NsdfError) as e:       # not loaded yet
+        sdf.query(d)
+    assert e.value.status == 3
+    sdf.load(blob)
+    empty = torch.zeros(0, 4, device="cuda")
+    sdf.query(empty)                                # n = 0: no-op
+    big = torch.zeros(9, 4, device="cuda")
+    with pytest.raises(nsdf.NsdfError) as e:       # misaligned (offset by one float)
+        nsdf.nsdf_query(sdf.ctx, big.view(-1)[1:33].view(8, 4), torch.empty(8, 4, device="cuda"))
+    assert e.value.status == 2
+    with pytest.raises(nsdf.NsdfError):            # wrong blob size
+        nsdf.nsdf_load_weights(sdf.ctx, 0, torch.zeros(10, device="cuda"))
+    with pytest.raises(nsdf.NsdfError):            # singular transform
+        sdf.collide(d, 0.002, T=np.zeros((4, 4)))
+    nsdf.nsdf_sync_status(sdf.ctx)
+    sdf.close()
+
+
+def test_device_blob_load_equals_host_blob_load(nsdf):
+    blob = synth.geometric_init(BODY, 0)
+    pts = torch.from_numpy(synth.body_scale_points(2048, 7)).cuda()
+    a = nsdf.NeuralSDF(BODY, nsdf.NSDF_FP32).load(blob)
+    b = nsdf.NeuralSDF(BODY, nsdf.NSDF_FP32).load(torch.from_numpy(blob).cuda())
+    oa, ob = a.query(pts), b.query(pts)
+    torch.cuda.synchronize()
+    assert torch.equal(oa, ob)
+    a.close()
+    b.close()
+
+
+def test_full_size_sampled_parity(nsdf):
+    """1,048,576 body-scale points in the benchmark's launch; oracle on a sample."""
+    blob = synth.geometric_init(BODY, 0)
+    n = 1 << 20
+    pts = synth.body_scale_points(n, 1)
+    sdf = nsdf.NeuralSDF(BODY, nsdf.NSDF_FP32).load(blob)
+    d = torch.from_numpy(pts).cuda()
+    out_pts = torch.empty_like(d)
+    out_ns = torch.empty_like(d)
+    out_hit = torch.empty(n, dtype=torch.uint8, device="cuda")
+    sdf.collide(d, 0.002, out_pts=out_pts, out_n_sdf=out_ns, out_hit=out_hit)
+    torch.cuda.synchronize()
+    sdf.close()
+    idx = np.sort(synth.Stream(99).u64(2048) % np.uint64(n)).astype(np.int64)
+    idx[-1] = n - 1
+    f, N, hit, x = mlp.collide(blob, BODY, pts[idx], 0.002)
+    check_collide(f, N, hit, x, 0.002, out_pts.cpu().numpy()[idx], out_ns.cpu().numpy()[idx],
+                  out_hit.cpu().numpy()[idx], pts[idx])
