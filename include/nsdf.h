@@ -55,8 +55,11 @@ typedef enum {
 } nsdf_status;
 
 typedef enum {
-  NSDF_FP32 = 0,  /* FP32 CUDA-core arithmetic throughout                     */
-  NSDF_BF16 = 1   /* hidden-layer products on BF16 tensor cores, FP32 accumulate */
+  NSDF_FP32 = 0,  /* FP32 CUDA-core arithmetic throughout                      */
+  NSDF_BF16 = 1,  /* hidden-layer products on BF16 tensor cores, FP32 accumulate */
+  NSDF_FP16 = 2   /* hidden-layer products on FP16 tensor cores, FP32 accumulate:
+                     same speed as BF16, 3 more significand bits; activations and
+                     weights must stay within FP16 range (|x| < 65504)         */
 } nsdf_precision;
 
 /*
@@ -86,8 +89,8 @@ size_t nsdf_num_params(const nsdf_arch *arch);
 /*
  * Create a context for n_nets networks of the same shape on the current
  * device.  Synchronous.  Fails with NSDF_ERR_UNSUPPORTED when no kernel of
- * this build handles (arch, prec): FP32 takes widths 32..512 in multiples of
- * 32; BF16 takes width 512 (the body-scale network) and width 64.
+ * this build handles (arch, prec): FP32 takes widths 32, 64, 128, 256 and
+ * 512; BF16 and FP16 take width 512 with at least two hidden layers.
  */
 nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets,
                         nsdf_ctx **out);
@@ -98,7 +101,7 @@ nsdf_status nsdf_destroy(nsdf_ctx *ctx);
 /*
  * Load the packed FP32 blob `w` (n_floats == nsdf_num_params) of network
  * `net`.  The library keeps its own converted copies (transposed, padded,
- * BF16 where the precision asks); the caller keeps `w`.  w_is_device
+ * 16-bit where the precision asks); the caller keeps `w`.  w_is_device
  * selects whether `w` is a device or a host pointer; with a host pointer the
  * call returns after the copy has been taken.
  */

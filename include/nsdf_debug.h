@@ -1,0 +1,35 @@
+/*
+ * nsdf_debug.h - test-only controls of the nsdf library's failure path.
+ *
+ * The tensor-core query kernel hands work between its producer, MMA and
+ * epilogue warps through mbarriers.  Every wait is bounded: after
+ * `wait_budget_cycles` SM clock cycles without progress the kernel records a
+ * timeout in the context's error word, lets the copies and products it has
+ * in flight finish, frees its tensor memory and returns;
+ * nsdf_sync_status() then reports NSDF_ERR_TIMEOUT and the context stays
+ * usable.  Nothing in the paper corresponds to this; it exists so that a
+ * test can exercise the timeout path without faulting or hanging a GPU.
+ */
+#ifndef NSDF_DEBUG_H
+#define NSDF_DEBUG_H
+
+#include "nsdf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * drop_load >= 0: the producer skips that weight-panel load (counted from 0
+ * within one launch), so the consumer's wait for it runs out.  -1 restores
+ * normal operation.  wait_budget_cycles > 0 bounds every mbarrier wait
+ * (default 4e9 cycles, about two seconds).  Applies to later launches of
+ * this context's BF16 query; host-side only, no device work.
+ */
+nsdf_status nsdf_debug_inject(nsdf_ctx *ctx, int drop_load, long long wait_budget_cycles);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSDF_DEBUG_H */

@@ -17,13 +17,13 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (NSDF_BF16, NSDF_FP32, NSDF_RAW_GRADIENT, nsdf_arch)
+from ._abi import (NSDF_BF16, NSDF_FP16, NSDF_FP32, NSDF_RAW_GRADIENT, nsdf_arch)
 
 __all__ = [
-    "NsdfError", "NSDF_FP32", "NSDF_BF16", "NSDF_RAW_GRADIENT", "make_arch",
+    "NsdfError", "NSDF_FP32", "NSDF_BF16", "NSDF_FP16", "NSDF_RAW_GRADIENT", "make_arch",
     "nsdf_num_params", "nsdf_create", "nsdf_destroy", "nsdf_load_weights",
     "nsdf_query", "nsdf_collide", "nsdf_backward", "nsdf_query_grouped",
-    "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status",
+    "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status", "nsdf_debug_inject",
     "nsdf_status_string", "NeuralSDF", "library",
 ]
 
@@ -142,6 +142,12 @@ def nsdf_cloth_step(x, x_prev, nx, ny, hx, hz, k_over_m, g, dt, stream=None):
     _check(library().nsdf_cloth_step(_ptr(x), _ptr(x_prev), int(nx), int(ny), float(hx),
                                      float(hz), float(k_over_m), float(g), float(dt),
                                      _stream(stream)), "nsdf_cloth_step")
+
+
+def nsdf_debug_inject(ctx, drop_load=-1, wait_budget_cycles=4_000_000_000):
+    """Test-only: drop one weight-panel load and/or shorten the kernel's bounded waits."""
+    _check(library().nsdf_debug_inject(ctx, int(drop_load), int(wait_budget_cycles)),
+           "nsdf_debug_inject")
 
 
 def nsdf_sync_status(ctx, stream=None):

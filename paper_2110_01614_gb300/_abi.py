@@ -22,6 +22,7 @@ NSDF_ERR_TIMEOUT = 7
 
 NSDF_FP32 = 0
 NSDF_BF16 = 1
+NSDF_FP16 = 2
 NSDF_RAW_GRADIENT = 1
 
 
@@ -52,6 +53,7 @@ SIGNATURES = {
                               ctypes.c_float, _P]),
     "nsdf_sync_status": (_ST, [_P, _P]),
     "nsdf_status_string": (ctypes.c_char_p, [_ST]),
+    "nsdf_debug_inject": (_ST, [_P, ctypes.c_int, ctypes.c_longlong]),
 }
 
 _lib = None

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "nsdf_internal.h"
+#include "nsdf_debug.h"
 
 using namespace nsdf;
 
@@ -80,8 +81,23 @@ struct PackPlan {
   int out[kMaxLayers];
 };
 
+struct PackTargets {
+  float *w0, *bias, *fwd_t, *bwd, *wout, *bout;
+  uint16_t *fwd16, *bwd16;
+  int fp16;   // 16-bit copies as FP16 (1) or BF16 (0)
+};
+
+__device__ __forceinline__ uint16_t to16(float v, int fp16) {
+  if (fp16) {
+    __half h = __float2half_rn(v);
+    return *reinterpret_cast<uint16_t *>(&h);
+  }
+  __nv_bfloat16 b = __float2bfloat16_rn(v);
+  return *reinterpret_cast<uint16_t *>(&b);
+}
+
 // Converts the packed FP32 blob into every device layout the kernels read.
-__global__ void pack_weights_kernel(const float *__restrict__ blob, PackPlan plan, NetDevice net) {
+__global__ void pack_weights_kernel(const float *__restrict__ blob, PackPlan plan, PackTargets net) {
   const int W = plan.width, L = plan.n_hidden;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -110,8 +126,8 @@ __global__ void pack_weights_kernel(const float *__restrict__ blob, PackPlan pla
     net.fwd_t[o] = w_cr;   // [k=r][n=c] = W_l[n][k]
     net.bwd[o] = w_rc;     // [n=r][k=c] = W_l[n][k]
     if (net.fwd16) {
-      net.fwd16[o] = __float2bfloat16_rn(w_rc);   // [n=r][k=c]
-      net.bwd16[o] = __float2bfloat16_rn(w_cr);   // [k=r][n=c]
+      net.fwd16[o] = to16(w_rc, net.fp16);   // [n=r][k=c]
+      net.bwd16[o] = to16(w_cr, net.fp16);   // [k=r][n=c]
     }
   }
 }
@@ -138,6 +154,9 @@ struct nsdf_ctx {
   float *pipe_scratch[2] = {nullptr, nullptr};
   size_t pipe_scratch_bytes = 0;
   int64_t chunk = 0;
+  // bounded waits and test-only fault injection (see include/nsdf_debug.h)
+  long long wait_budget = 4000000000LL;   // ~2 s of SM clock per mbarrier wait
+  int drop_load = -1;
 };
 
 namespace {
@@ -161,15 +180,16 @@ nsdf_status ctx_alloc(nsdf_ctx *ctx, T **p, size_t count) {
   return NSDF_OK;
 }
 
-bool use_bf16(const nsdf_ctx *ctx) { return ctx->prec == NSDF_BF16; }
+// BF16 and FP16 contexts share the 16-bit tensor-core kernel.
+bool use_bf16(const nsdf_ctx *ctx) { return ctx->prec == NSDF_BF16 || ctx->prec == NSDF_FP16; }
 
 int query_grid(const nsdf_ctx *ctx, int64_t n) {
-  if (use_bf16(ctx)) return query_bf16_grid(ctx->arch.width, n, ctx->num_sms);
+  if (use_bf16(ctx)) return query_tc16_grid(ctx->arch.width, n, ctx->num_sms);
   return query_fp32_grid(ctx->arch.width, n, ctx->num_sms);
 }
 
 size_t query_scratch(const nsdf_ctx *ctx, int grid) {
-  if (use_bf16(ctx)) return query_bf16_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
+  if (use_bf16(ctx)) return query_tc16_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
   return query_fp32_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
 }
 
@@ -197,10 +217,13 @@ void fill_net(const nsdf_ctx *ctx, int net, QueryParams &p) {
   p.skip = ctx->arch.skip_layer;
   p.beta = ctx->arch.beta;
   p.err = ctx->d_err;
+  p.wait_budget = ctx->wait_budget;
+  p.drop_load = ctx->drop_load;
 }
 
-cudaError_t launch_query(const nsdf_ctx *ctx, const QueryParams &p, cudaStream_t s) {
-  if (use_bf16(ctx)) return launch_query_bf16(p, ctx->num_sms, s);
+cudaError_t launch_query(const nsdf_ctx *ctx, int net, const QueryParams &p, cudaStream_t s) {
+  if (use_bf16(ctx))
+    return launch_query_tc16_net(p, ctx->nets[net], ctx->prec == NSDF_FP16, ctx->num_sms, s);
   return launch_query_fp32(p, ctx->num_sms, s);
 }
 
@@ -280,7 +303,7 @@ nsdf_status collide_host(nsdf_ctx *ctx, QueryParams base, const float *pts, int6
     p.out_n_sdf = out_n_sdf ? d_nsdf : nullptr;
     p.out_hit = out_hit ? d_hit : nullptr;
     p.scratch = ctx->pipe_scratch[b];
-    e = launch_query(ctx, p, ps);
+    e = launch_query(ctx, 0, p, ps);
     if (e != cudaSuccess) return map_err(e);
     if (out_pts) {
       e = cudaMemcpyAsync(out_pts + 4 * c0, d_out, (size_t)m * 16, cudaMemcpyDeviceToHost, ps);
@@ -333,9 +356,9 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
   if (!out) return NSDF_ERR_INVALID_ARG;
   *out = nullptr;
   if (!arch_valid(arch) || n_nets < 1 || n_nets > 4096) return NSDF_ERR_INVALID_ARG;
-  if (prec != NSDF_FP32 && prec != NSDF_BF16) return NSDF_ERR_INVALID_ARG;
+  if (prec != NSDF_FP32 && prec != NSDF_BF16 && prec != NSDF_FP16) return NSDF_ERR_INVALID_ARG;
   if (prec == NSDF_FP32 && !query_fp32_supported(arch->width)) return NSDF_ERR_UNSUPPORTED;
-  if (prec == NSDF_BF16 && !query_bf16_supported(arch->width, arch->n_hidden, arch->skip_layer))
+  if (prec != NSDF_FP32 && !query_tc16_supported(arch->width, arch->n_hidden, arch->skip_layer))
     return NSDF_ERR_UNSUPPORTED;
   nsdf_ctx *ctx = new (std::nothrow) nsdf_ctx;
   if (!ctx) return NSDF_ERR_OOM;
@@ -360,7 +383,7 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
     if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd, hid);
     if (st == NSDF_OK) st = ctx_alloc(ctx, &d.wout, (size_t)W);
     if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bout, 4);
-    if (st == NSDF_OK && prec == NSDF_BF16) {
+    if (st == NSDF_OK && prec != NSDF_FP32) {
       st = ctx_alloc(ctx, &d.fwd16, hid);
       if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd16, hid);
     }
@@ -423,7 +446,10 @@ nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w, size_t n_f
     plan.boff[l] = off;
     off += layer_out(a, l);
   }
-  pack_weights_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(src, plan, ctx->nets[net]);
+  const NetDevice &d = ctx->nets[net];
+  PackTargets tg{d.w0, d.bias, d.fwd_t, d.bwd, d.wout, d.bout, d.fwd16, d.bwd16,
+                 ctx->prec == NSDF_FP16 ? 1 : 0};
+  pack_weights_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(src, plan, tg);
   cudaError_t e = last_err();
   if (tmp) {
     cudaError_t e2 = cudaStreamSynchronize(s);
@@ -431,6 +457,8 @@ nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w, size_t n_f
     if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) return map_err(e);
+  if (use_bf16(ctx) && !make_tc16_tmaps(ctx->nets[net], a.width, a.n_hidden, ctx->prec == NSDF_FP16))
+    return NSDF_ERR_CUDA;
   ctx->nets[net].loaded = true;
   return NSDF_OK;
 }
@@ -455,7 +483,7 @@ nsdf_status nsdf_query(nsdf_ctx *ctx, const float *pts, int64_t n, float *out_n_
   nsdf_status st = ensure_scratch(ctx, query_scratch(ctx, grid));
   if (st != NSDF_OK) return st;
   p.scratch = ctx->scratch;
-  return map_err(launch_query(ctx, p, s));
+  return map_err(launch_query(ctx, 0, p, s));
 }
 
 nsdf_status nsdf_collide(nsdf_ctx *ctx, const float *pts, int64_t n, float eps, const float *T,
@@ -488,7 +516,7 @@ nsdf_status nsdf_collide(nsdf_ctx *ctx, const float *pts, int64_t n, float eps, 
   st = ensure_scratch(ctx, query_scratch(ctx, grid));
   if (st != NSDF_OK) return st;
   p.scratch = ctx->scratch;
-  return map_err(launch_query(ctx, p, s));
+  return map_err(launch_query(ctx, 0, p, s));
 }
 
 nsdf_status nsdf_sync_status(nsdf_ctx *ctx, nsdf_stream stream) {
@@ -503,6 +531,13 @@ nsdf_status nsdf_sync_status(nsdf_ctx *ctx, nsdf_stream stream) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
     return NSDF_ERR_TIMEOUT;
   }
+  return NSDF_OK;
+}
+
+nsdf_status nsdf_debug_inject(nsdf_ctx *ctx, int drop_load, long long wait_budget_cycles) {
+  if (!ctx || wait_budget_cycles <= 0) return NSDF_ERR_INVALID_ARG;
+  ctx->drop_load = drop_load;
+  ctx->wait_budget = wait_budget_cycles;
   return NSDF_OK;
 }
 

@@ -2,8 +2,10 @@
 // nsdf library.  Nothing here is part of the public ABI (include/nsdf.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <cstddef>
 
@@ -28,9 +30,12 @@ struct NetDevice {
   float *bwd = nullptr;    // [n_hidden-1][width(n)][width(k)] = W_l[n][k]
   float *wout = nullptr;   // [width]      output weights (zero padded)
   float *bout = nullptr;   // [1]
-  // BF16 forms (tensor-core B operands, K-major)
-  __nv_bfloat16 *fwd16 = nullptr;  // [n_hidden-1][width(n)][width(k)] = W_l
-  __nv_bfloat16 *bwd16 = nullptr;  // [n_hidden-1][width(k)][width(n)] = W_l^T
+  // 16-bit forms (tensor-core B operands, K-major; BF16 or FP16 bits)
+  uint16_t *fwd16 = nullptr;  // [n_hidden-1][width(n)][width(k)] = W_l
+  uint16_t *bwd16 = nullptr;  // [n_hidden-1][width(k)][width(n)] = W_l^T
+  // TMA descriptors of fwd16 / bwd16 (16-bit contexts only)
+  CUtensorMap tmap_fwd;
+  CUtensorMap tmap_bwd;
   bool loaded = false;
 };
 
@@ -49,12 +54,17 @@ struct QueryParams {
   float R[9];          // T[:3,:3]
   // network
   const float *w0, *bias, *fwd_t, *bwd, *wout, *bout;
-  const __nv_bfloat16 *fwd16, *bwd16;
+  const uint16_t *fwd16, *bwd16;
   int width, n_hidden, skip;
   float beta;
   // per-CTA scratch and the context's error word
   float *scratch;
   int *err;
+  // bounded waits: clock cycles one mbarrier wait may spin before the kernel
+  // records kDevTimeout and unwinds; drop_load >= 0 skips that weight load
+  // (fault injection for tests of the timeout path; -1 in normal use)
+  long long wait_budget;
+  int drop_load;
 };
 
 // Launchers (return a cudaError_t from the launch).
@@ -63,9 +73,11 @@ size_t query_fp32_scratch_bytes(int width, int n_hidden, int grid);
 int query_fp32_grid(int width, int64_t n, int num_sms);
 bool query_fp32_supported(int width);
 
-bool query_bf16_supported(int width, int n_hidden, int skip);
-cudaError_t launch_query_bf16(const QueryParams &p, int num_sms, cudaStream_t s);
-size_t query_bf16_scratch_bytes(int width, int n_hidden, int grid);
-int query_bf16_grid(int width, int64_t n, int num_sms);
+bool query_tc16_supported(int width, int n_hidden, int skip);
+bool make_tc16_tmaps(NetDevice &net, int width, int n_hidden, bool fp16);
+cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bool fp16,
+                                  int num_sms, cudaStream_t s);
+size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid);
+int query_tc16_grid(int width, int64_t n, int num_sms);
 
 }  // namespace nsdf

@@ -1,0 +1,652 @@
+// 16-bit tensor-core form of the fused collision query (width-512 networks):
+// BF16 or FP16 operands (one template), FP32 accumulation in TMEM.
+//
+// One persistent CTA per SM walks tiles of 128 points.  Per tile the whole
+// query of Sec. 3.2 runs on chip:
+//   * L0 (K = 3) on CUDA cores in the epilogue warps,
+//   * each hidden layer z_l = W_l x_l (Eq. 1) as 64 tcgen05.mma
+//     (M=128, N=256, K=16; 16-bit x 16-bit -> FP32) into TMEM, A = the
+//     activation tile resident in shared memory (128 x 512, 128-byte
+//     swizzled K-major), B = weight panels streamed by TMA through a
+//     3-stage ring,
+//   * the epilogue warps read z from TMEM (tcgen05.ld), add the bias and
+//     write softplus_beta(z) back as the next A operand, and park
+//     sigmoid(beta z) (the slope the reverse chain needs) in a per-CTA
+//     scratch slab (16-bit, lane-contiguous, L2-resident),
+//   * the skip connection's input columns p/sqrt(2) never pass through the
+//     16-bit operands: their product with W_s is added in FP32 on CUDA
+//     cores, and their gradient is accumulated in FP32 from delta_s,
+//   * the output unit f = w_out . h_7 is an FP32 dot in the last epilogue,
+//   * the Jacobian-transpose chain (back-propagation of Sec. 3.2):
+//     delta_l = sigmoid(beta z_l) * g_l, g_{l-1} = W_l^T delta_l as the same
+//     tcgen05 products against the transposed weights, the skip
+//     connection's 1/sqrt(2) split, and grad f = W_0^T delta_0 in FP32,
+//   * Eq. 2, the test f < eps and the contact point of Eq. 3 (with the
+//     rigid transform of Sec. 4.2) in the final epilogue; float4 stores.
+//
+// Warp roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
+// TMEM owner, warps 2..9 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31;
+// warps 2..5 take columns 0..255 of every layer, warps 6..9 columns
+// 256..511).  Producer, MMA and epilogue hand over through mbarriers; every
+// wait is bounded (QueryParams::wait_budget cycles) and on expiry the kernel
+// records kDevTimeout, drains what it has in flight and returns.
+
+#include <cudaTypedefs.h>
+
+#include "nsdf_internal.h"
+
+namespace nsdf {
+namespace {
+
+constexpr int kW = 512;                    // network width handled here
+constexpr int kM = 128;                    // points per tile (MMA M, TMEM lanes)
+constexpr int kN = 256;                    // MMA N (one half of a layer)
+constexpr int kKAtom = 64;                 // K elements per 128-byte swizzle atom
+constexpr int kStages = 3;
+constexpr int kStageBytes = kN * kKAtom * 2;          // 32 KB weight panel
+constexpr int kABytes = kM * kW * 2;                  // 128 KB activation tile
+constexpr int kAtomBytes = kM * kKAtom * 2;           // 16 KB: one K atom of A
+constexpr int kLoadsPerLayer = (kW / kN) * (kW / kKAtom);   // 16
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr float kInvSqrt2 = 0.70710678118654752f;
+
+// shared-memory map (bytes from a 1024-aligned base)
+constexpr int kOffA = 0;
+constexpr int kOffB = kOffA + kABytes;
+constexpr int kOffBar = kOffB + kStages * kStageBytes;
+// barriers: full[kStages], empty[kStages], a_ready, d_full, mma_done, x_full, x_empty
+constexpr int kNumBars = 2 * kStages + 5;
+constexpr int kOffTmemSlot = kOffBar + 8 * kNumBars;
+constexpr int kOffAbort = kOffTmemSlot + 4;
+constexpr int kOffExch = ((kOffAbort + 4 + 15) / 16) * 16;   // float4 [kM]
+constexpr int kSmemBytes = kOffExch + kM * 16;
+static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+// Instruction descriptor of tcgen05.mma .kind::f16: D F32 (bits 4-5 = 1),
+// A and B of the same 16-bit format, both K-major, N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+// Operand format code (bits 7-9 and 10-12): 0 = F16, 1 = BF16.
+template <bool kF16>
+struct Op {
+  static constexpr uint32_t fmt = kF16 ? 0u : 1u;
+  static constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) |
+                                    ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+  static __device__ __forceinline__ uint32_t pack(float lo, float hi) {
+    if constexpr (kF16) {
+      __half2 t = __floats2half2_rn(lo, hi);
+      return *reinterpret_cast<uint32_t *>(&t);
+    } else {
+      __nv_bfloat162 t = __floats2bfloat162_rn(lo, hi);
+      return *reinterpret_cast<uint32_t *>(&t);
+    }
+  }
+  static __device__ __forceinline__ float2 unpack(uint32_t u) {
+    if constexpr (kF16) {
+      __half2 t = *reinterpret_cast<__half2 *>(&u);
+      return __half22float2(t);
+    } else {
+      __nv_bfloat162 t = *reinterpret_cast<__nv_bfloat162 *>(&u);
+      return __bfloat1622float2(t);
+    }
+  }
+};
+
+// Shared-memory matrix descriptor for a K-major operand in the 128-byte
+// swizzle layout: 8-row groups 1024 bytes apart (SBO), descriptor version 1
+// (bits 46-47), layout type 2 = SWIZZLE_128B (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity.  Gives up (false) when
+// the budget of clock cycles is spent or another role has aborted.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget,
+                                       volatile int *abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+      : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+
+// Store 32 16-bit values (16 packed words) of row r, columns k0..k0+31, into
+// the 128-byte-swizzled K-major activation tile.
+__device__ __forceinline__ void store_a_chunk(uint8_t *A, int r, int k0, const uint32_t (&w)[16]) {
+  const int atom = k0 >> 6;
+  const int j0 = (k0 & 63) >> 3;
+  uint8_t *row = A + atom * kAtomBytes + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int phys = (j0 + t) ^ (r & 7);
+    uint4 v = make_uint4(w[4 * t], w[4 * t + 1], w[4 * t + 2], w[4 * t + 3]);
+    *reinterpret_cast<uint4 *>(row + phys * 16) = v;
+  }
+}
+
+// softplus_beta and sigmoid(beta z) from one exponential (fast forms: the
+// value is rounded to 16 bits next, the slope feeds a 16-bit operand).
+__device__ __forceinline__ void act(float z, float beta, float inv_beta, float &h, float &s) {
+  const float e = __expf(-beta * fabsf(z));
+  const float one_e = 1.0f + e;
+  h = fmaxf(z, 0.0f) + __logf(one_e) * inv_beta;
+  const float r = __fdividef(1.0f, one_e);
+  s = (z >= 0.0f) ? r : e * r;
+}
+
+struct Roles {
+  int warp, lane;
+};
+
+template <bool kF16>
+__global__ void __launch_bounds__(kThreads, 1)
+    query_tc16_kernel(const QueryParams prm, const __grid_constant__ CUtensorMap tmap_fwd,
+                      const __grid_constant__ CUtensorMap tmap_bwd) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = smem_raw;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if ((smem_u32(smem) & 1023u) != 0) {   // the swizzled layouts need a 1024-aligned base
+    if (threadIdx.x == 0) atomicExch(prm.err, kDevTimeout);
+    return;
+  }
+  uint8_t *A = smem + kOffA;
+  const uint32_t sA = smem_u32(A), sB = smem_u32(smem + kOffB);
+  const uint32_t bar0 = smem_u32(smem + kOffBar);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
+  const uint32_t a_ready = bar0 + 8u * (2 * kStages);
+  const uint32_t d_full = a_ready + 8u;
+  const uint32_t mma_done = d_full + 8u;
+  const uint32_t x_full = mma_done + 8u;    // column-half 1 has published its partial sums
+  const uint32_t x_empty = x_full + 8u;     // column-half 0 has consumed them
+  volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + kOffTmemSlot);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kOffAbort);
+  float4 *exch = reinterpret_cast<float4 *>(smem + kOffExch);
+
+  const int L = prm.n_hidden;
+  const int G = 2 * (L - 1);                   // tensor-core layers per tile
+  const int64_t ntiles = (prm.n + kM - 1) / kM;
+  const long long budget = prm.wait_budget;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(a_ready, kEpiWarps);
+    mbar_init(d_full, 1);
+    mbar_init(mma_done, 1);
+    mbar_init(x_full, kEpiWarps / 2);
+    mbar_init(x_empty, kEpiWarps / 2);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(smem + kOffTmemSlot)),
+                 "r"(kW));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto fail = [&]() {
+    atomicExch(prm.err, kDevTimeout);
+    *abort_flag = 1;
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_parity[kStages];
+      bool issued[kStages];
+      for (int s = 0; s < kStages; ++s) issued[s] = false, issued_parity[s] = 0;
+      int64_t load_idx = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        for (int li = 0; ok && li < G; ++li) {
+          const bool fwd = li < L - 1;
+          const int l = fwd ? li + 1 : G - li;           // network layer of this product
+          const CUtensorMap *map = fwd ? &tmap_fwd : &tmap_bwd;
+          const int rowbase = (l - 1) * kW;
+          for (int ld = 0; ld < kLoadsPerLayer; ++ld, ++load_idx) {
+            if (!mbar_wait(empty_bar(stage), phase ^ 1u, budget, abort_flag)) {
+              fail();
+              ok = false;
+              break;
+            }
+            const int nh = ld / (kW / kKAtom), kb = ld % (kW / kKAtom);
+            if (load_idx != prm.drop_load) {
+              mbar_expect_tx(full_bar(stage), kStageBytes);
+              tma_load_2d(sB + stage * kStageBytes, map, kb * kKAtom, rowbase + nh * kN,
+                          full_bar(stage));
+              issued[stage] = true;
+              issued_parity[stage] = phase;
+            }
+            if (++stage == kStages) stage = 0, phase ^= 1u;
+          }
+        }
+      }
+      // drain: every issued load must land before the CTA may exit
+      for (int s = 0; s < kStages; ++s) {
+        if (issued[s]) {
+          volatile int no_abort = 0;
+          if (!mbar_wait(full_bar(s), issued_parity[s], budget, &no_abort)) fail();
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, a_phase = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        for (int li = 0; ok && li < G; ++li) {
+          if (!mbar_wait(a_ready, a_phase, budget, abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          a_phase ^= 1u;
+          tc_fence_after();
+          for (int ld = 0; ld < kLoadsPerLayer; ++ld) {
+            if (!mbar_wait(full_bar(stage), phase, budget, abort_flag)) {
+              fail();
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const int nh = ld / (kW / kKAtom), kb = ld % (kW / kKAtom);
+            const uint32_t d = tmem + (uint32_t)(nh * kN);
+            const uint32_t a_atom = sA + kb * kAtomBytes;
+            const uint32_t b_stage = sB + stage * kStageBytes;
+#pragma unroll
+            for (int ks = 0; ks < kKAtom / 16; ++ks) {
+              mma_16(d, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32),
+                     Op<kF16>::idesc, (kb | ks) != 0 ? 1u : 0u);
+            }
+            mma_commit(empty_bar(stage));
+            if (++stage == kStages) stage = 0, phase ^= 1u;
+          }
+          if (ok) mma_commit(d_full);
+        }
+      }
+      // drain: no product may still be writing TMEM when it is freed
+      mma_commit(mma_done);
+      volatile int no_abort = 0;
+      if (!mbar_wait(mma_done, 0, budget, &no_abort)) fail();
+    }
+  } else {
+    // ---------------- epilogue warps ----------------
+    const int e = warp - 2;
+    const int q = warp & 3;                  // TMEM lane quarter
+    const int ch = e >> 2;                   // column half
+    const int r = 32 * q + lane;             // row of the tile = TMEM lane
+    const uint32_t t_row = tmem + ((uint32_t)(32 * q) << 16);
+    const float beta = prm.beta, inv_beta = 1.0f / prm.beta;
+    const int skip = prm.skip;
+    const int nshort = kW - 3;
+    // W_s[:, nshort + j] (j = 0..2): the skip layer's weights on p, FP32, from
+    // the transposed copy (row k = nshort + j holds W_s[n][k] over n)
+    const float *wsk = skip > 0 ? prm.fwd_t + ((size_t)(skip - 1) * kW + nshort) * kW : prm.fwd_t;
+    uint8_t *slab = reinterpret_cast<uint8_t *>(prm.scratch) +
+                    (size_t)blockIdx.x * (size_t)(L - 1) * 2 * 32 * kM * 16;
+    auto slab_chunk = [&](int l, int j) -> uint4 * {   // 8 slopes (16 B) of row r
+      return reinterpret_cast<uint4 *>(slab + ((((size_t)l * 2 + ch) * 32 + j) * kM + r) * 16);
+    };
+    uint32_t d_phase = 0, x_phase = 0;
+    bool ok = true;
+    auto arrive_a = [&]() {
+      fence_proxy_async();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(a_ready);
+    };
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      const int64_t idx = tile * kM + r;
+      float4 pw = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (idx < prm.n) pw = prm.pts[idx];
+      float px = pw.x, py = pw.y, pz = pw.z;
+      if (prm.has_T) {
+        const float *t = prm.Ti;
+        px = t[0] * pw.x + t[1] * pw.y + t[2] * pw.z + t[3];
+        py = t[4] * pw.x + t[5] * pw.y + t[6] * pw.z + t[7];
+        pz = t[8] * pw.x + t[9] * pw.y + t[10] * pw.z + t[11];
+      }
+      float fpart = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+
+      // ---- L0 on CUDA cores ----
+      {
+        const bool feeds_skip = (skip == 1);
+        for (int cc = 0; cc < 8; ++cc) {
+          const int c0 = ch * 256 + cc * 32;
+          uint32_t hw[16], sw[16];
+#pragma unroll
+          for (int i = 0; i < 32; i += 2) {
+            float hv[2], sv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int c = c0 + i + u;
+              const float z = fmaf(prm.w0[3 * c], px, fmaf(prm.w0[3 * c + 1], py,
+                                   fmaf(prm.w0[3 * c + 2], pz, prm.bias[c])));
+              act(z, beta, inv_beta, hv[u], sv[u]);
+              if (feeds_skip) hv[u] = (c < nshort) ? hv[u] * kInvSqrt2 : 0.0f;
+            }
+            hw[i / 2] = Op<kF16>::pack(hv[0], hv[1]);
+            sw[i / 2] = Op<kF16>::pack(sv[0], sv[1]);
+          }
+          store_a_chunk(A, r, c0, hw);
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            *slab_chunk(0, cc * 4 + t) = make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]);
+        }
+        arrive_a();
+      }
+
+      // ---- hidden layers L1 .. L{L-1} (forward) ----
+      for (int l = 1; ok && l < L; ++l) {
+        if (!mbar_wait(d_full, d_phase, budget, abort_flag)) { fail(); ok = false; break; }
+        d_phase ^= 1u;
+        tc_fence_after();
+        const bool last = (l == L - 1);
+        const bool feeds_skip = (skip > 0 && l == skip - 1);
+        const bool at_skip = (skip > 0 && l == skip);
+        const float *b = prm.bias + (size_t)l * kW;
+        for (int cc = 0; cc < 8; ++cc) {
+          const int c0 = ch * 256 + cc * 32;
+          float v[32];
+          tmem_ld32(t_row + (uint32_t)c0, v);
+          uint32_t hw[16], sw[16];
+#pragma unroll
+          for (int i = 0; i < 32; i += 2) {
+            float hv[2], sv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int c = c0 + i + u;
+              float z = v[i + u] + __ldg(b + c);
+              if (at_skip) {   // the input columns p / sqrt(2), in FP32
+                z = fmaf(kInvSqrt2, fmaf(__ldg(wsk + c), px, fmaf(__ldg(wsk + kW + c), py,
+                                         __ldg(wsk + 2 * kW + c) * pz)), z);
+              }
+              act(z, beta, inv_beta, hv[u], sv[u]);
+              if (last) {
+                const float wo = __ldg(prm.wout + c);
+                fpart = fmaf(wo, hv[u], fpart);
+                hv[u] = sv[u] * wo;                     // delta_{L-1}
+                if (skip == L - 1) {                     // delta_s feeds the direct term
+                  gx = fmaf(hv[u], __ldg(wsk + c) * kInvSqrt2, gx);
+                  gy = fmaf(hv[u], __ldg(wsk + kW + c) * kInvSqrt2, gy);
+                  gz = fmaf(hv[u], __ldg(wsk + 2 * kW + c) * kInvSqrt2, gz);
+                }
+              } else if (feeds_skip) {
+                hv[u] = (c < nshort) ? hv[u] * kInvSqrt2 : 0.0f;
+              }
+            }
+            hw[i / 2] = Op<kF16>::pack(hv[0], hv[1]);
+            sw[i / 2] = Op<kF16>::pack(sv[0], sv[1]);
+          }
+          store_a_chunk(A, r, c0, hw);
+          if (!last) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              *slab_chunk(l, cc * 4 + t) = make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]);
+          }
+        }
+        arrive_a();
+      }
+
+      // ---- Jacobian-transpose chain: layers L-1 .. 1 ----
+      for (int l = L - 1; ok && l >= 1; --l) {
+        if (!mbar_wait(d_full, d_phase, budget, abort_flag)) { fail(); ok = false; break; }
+        d_phase ^= 1u;
+        tc_fence_after();
+        const bool at_skip = (skip > 0 && l == skip);
+        const bool makes_skip_delta = (skip > 0 && l - 1 == skip);
+        const bool to_input = (l == 1);
+        for (int cc = 0; cc < 8; ++cc) {
+          const int c0 = ch * 256 + cc * 32;
+          float v[32];
+          tmem_ld32(t_row + (uint32_t)c0, v);
+          uint32_t sw[16];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const uint4 s4 = *slab_chunk(l - 1, cc * 4 + t);
+            sw[4 * t] = s4.x; sw[4 * t + 1] = s4.y; sw[4 * t + 2] = s4.z; sw[4 * t + 3] = s4.w;
+          }
+          uint32_t dw[16];
+#pragma unroll
+          for (int i = 0; i < 32; i += 2) {
+            const float2 s2 = Op<kF16>::unpack(sw[i / 2]);
+            float dv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int c = c0 + i + u;
+              float g = v[i + u];
+              if (at_skip) g = (c < nshort) ? g * kInvSqrt2 : 0.0f;
+              dv[u] = (u == 0 ? s2.x : s2.y) * g;
+              if (makes_skip_delta) {                   // direct path to the input
+                gx = fmaf(dv[u], __ldg(wsk + c) * kInvSqrt2, gx);
+                gy = fmaf(dv[u], __ldg(wsk + kW + c) * kInvSqrt2, gy);
+                gz = fmaf(dv[u], __ldg(wsk + 2 * kW + c) * kInvSqrt2, gz);
+              }
+              if (to_input) {
+                gx = fmaf(dv[u], __ldg(prm.w0 + 3 * c), gx);
+                gy = fmaf(dv[u], __ldg(prm.w0 + 3 * c + 1), gy);
+                gz = fmaf(dv[u], __ldg(prm.w0 + 3 * c + 2), gz);
+              }
+            }
+            dw[i / 2] = Op<kF16>::pack(dv[0], dv[1]);
+          }
+          if (!to_input) store_a_chunk(A, r, c0, dw);
+        }
+        if (!to_input) arrive_a();
+        else tc_fence_before();
+      }
+      if (!ok) break;
+
+      // ---- a7-a9: combine the two column halves, normalise, test, project ----
+      if (ch == 1) {
+        if (!mbar_wait(x_empty, x_phase ^ 1u, budget, abort_flag)) { fail(); ok = false; break; }
+        exch[r] = make_float4(gx, gy, gz, fpart);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(x_full);
+        x_phase ^= 1u;
+        continue;
+      }
+      if (!mbar_wait(x_full, x_phase, budget, abort_flag)) { fail(); ok = false; break; }
+      x_phase ^= 1u;
+      const float4 o = exch[r];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(x_empty);
+      if (idx < prm.n) {
+        gx += o.x; gy += o.y; gz += o.z;
+        const float f = fpart + o.w + __ldg(prm.bout);
+        const float nrm = sqrtf(gx * gx + gy * gy + gz * gz);
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (nrm >= 1e-20f) { nx = gx / nrm; ny = gy / nrm; nz = gz / nrm; }
+        if (!prm.collide) {
+          if (prm.raw_gradient) { nx = gx; ny = gy; nz = gz; }
+          prm.out_n_sdf[idx] = make_float4(nx, ny, nz, f);
+        } else {
+          if (prm.has_T) {
+            const float *R = prm.R;
+            const float wx = R[0] * nx + R[1] * ny + R[2] * nz;
+            const float wy = R[3] * nx + R[4] * ny + R[5] * nz;
+            const float wz = R[6] * nx + R[7] * ny + R[8] * nz;
+            nx = wx; ny = wy; nz = wz;
+          }
+          const bool hit = f < prm.eps;
+          float4 p = pw;
+          if (hit) {
+            const float d = prm.eps - f;
+            p.x = fmaf(d, nx, p.x); p.y = fmaf(d, ny, p.y); p.z = fmaf(d, nz, p.z);
+          }
+          if (prm.out_pts) prm.out_pts[idx] = p;
+          if (prm.out_n_sdf) prm.out_n_sdf[idx] = make_float4(nx, ny, nz, f);
+          if (prm.out_hit) prm.out_hit[idx] = hit ? 1 : 0;
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kW));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool encode_panel_map(CUtensorMap *map, void *base, int rows, bool fp16) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kW, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kW * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kKAtom, (cuuint32_t)kN};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool query_tc16_supported(int width, int n_hidden, int skip) {
+  (void)skip;
+  return width == kW && n_hidden >= 2;
+}
+
+bool make_tc16_tmaps(NetDevice &net, int width, int n_hidden, bool fp16) {
+  if (width != kW || n_hidden < 2) return false;
+  const int rows = (n_hidden - 1) * kW;
+  return encode_panel_map(&net.tmap_fwd, net.fwd16, rows, fp16) &&
+         encode_panel_map(&net.tmap_bwd, net.bwd16, rows, fp16);
+}
+
+int query_tc16_grid(int width, int64_t n, int num_sms) {
+  (void)width;
+  const int64_t tiles = (n + kM - 1) / kM;
+  return (int)(tiles < num_sms ? (tiles < 1 ? 1 : tiles) : num_sms);
+}
+
+size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid) {
+  (void)width;
+  return (size_t)grid * (size_t)(n_hidden - 1) * 2 * 32 * kM * 16;
+}
+
+template <bool kF16>
+cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(query_tc16_kernel<kF16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  const int grid = query_tc16_grid(p.width, p.n, num_sms);
+  query_tc16_kernel<kF16><<<grid, kThreads, kSmemBytes, s>>>(p, net.tmap_fwd, net.tmap_bwd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bool fp16,
+                                  int num_sms, cudaStream_t s) {
+  return fp16 ? launch_t<true>(p, net, num_sms, s) : launch_t<false>(p, net, num_sms, s);
+}
+
+}  // namespace nsdf
