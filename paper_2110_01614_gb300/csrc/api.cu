@@ -147,6 +147,8 @@ struct nsdf_ctx {
   float *scratch = nullptr;     // per-CTA slope slabs of the query kernels
   size_t scratch_bytes = 0;
   int *d_err = nullptr;         // device error word
+  float *bwd_partial = nullptr; // per-CTA weight-gradient partial sums of nsdf_backward
+  size_t bwd_partial_bytes = 0;
   // host-buffer pipeline
   cudaStream_t pipe[2] = {nullptr, nullptr};
   cudaEvent_t ev_start = nullptr, ev_done[2] = {nullptr, nullptr};
@@ -403,6 +405,7 @@ nsdf_status nsdf_destroy(nsdf_ctx *ctx) {
   cudaDeviceSynchronize();
   for (void *p : ctx->allocations) cudaFree(p);
   if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->bwd_partial) cudaFree(ctx->bwd_partial);
   if (ctx->stage) cudaFree(ctx->stage);
   for (int i = 0; i < 2; ++i) {
     if (ctx->pipe_scratch[i]) cudaFree(ctx->pipe_scratch[i]);
@@ -517,6 +520,69 @@ nsdf_status nsdf_collide(nsdf_ctx *ctx, const float *pts, int64_t n, float eps, 
   if (st != NSDF_OK) return st;
   p.scratch = ctx->scratch;
   return map_err(launch_query(ctx, 0, p, s));
+}
+
+nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n, const float *g_sdf,
+                          const float *g_grad, float *g_weights, float *g_pts, nsdf_stream stream) {
+  if (!ctx || n < 0) return NSDF_ERR_INVALID_ARG;
+  if (!ctx->nets[0].loaded) return NSDF_ERR_NOT_LOADED;
+  const nsdf_arch &a = ctx->arch;
+  const int64_t n_params = (int64_t)nsdf_num_params(&a);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    if (g_weights) return map_err(cudaMemsetAsync(g_weights, 0, sizeof(float) * n_params, s));
+    return NSDF_OK;
+  }
+  if (!pts || !g_sdf || (!g_weights && !g_pts)) return NSDF_ERR_INVALID_ARG;
+  if (!aligned16(pts) || (g_grad && !aligned16(g_grad)) || (g_pts && !aligned16(g_pts)))
+    return NSDF_ERR_MISALIGNED;
+  if (!g_grad && !g_weights) {
+    // first order only: dL/dp = g_sdf * grad f, through the FP32 query kernel
+    if (!query_fp32_supported(a.width)) return NSDF_ERR_UNSUPPORTED;
+    QueryParams p{};
+    fill_net(ctx, 0, p);
+    p.pts = reinterpret_cast<const float4 *>(pts);
+    p.n = n;
+    p.grad_scale = g_sdf;
+    p.out_grad = reinterpret_cast<float4 *>(g_pts);
+    const int grid = query_fp32_grid(a.width, n, ctx->num_sms);
+    nsdf_status st = ensure_scratch(ctx, query_fp32_scratch_bytes(a.width, a.n_hidden, grid));
+    if (st != NSDF_OK) return st;
+    p.scratch = ctx->scratch;
+    return map_err(launch_query_fp32(p, ctx->num_sms, s));
+  }
+  if (!backward_supported(a.width, a.n_hidden, n_params)) return NSDF_ERR_UNSUPPORTED;
+  int64_t woff[65], boff[65];
+  int out[65];
+  int64_t off = 0;
+  for (int l = 0; l <= a.n_hidden; ++l) {
+    out[l] = layer_out(a, l);
+    woff[l] = off;
+    off += (int64_t)layer_out(a, l) * layer_in(a, l);
+    boff[l] = off;
+    off += layer_out(a, l);
+  }
+  const int grid = backward_grid(n, ctx->num_sms);
+  if (g_weights) {
+    const size_t need = sizeof(float) * (size_t)grid * n_params;
+    if (need > ctx->bwd_partial_bytes) {
+      if (ctx->bwd_partial) cudaFree(ctx->bwd_partial);
+      ctx->bwd_partial = nullptr;
+      ctx->bwd_partial_bytes = 0;
+      void *q = nullptr;
+      if (cudaMalloc(&q, need) != cudaSuccess) {
+        cudaGetLastError();
+        return NSDF_ERR_OOM;
+      }
+      ctx->bwd_partial = static_cast<float *>(q);
+      ctx->bwd_partial_bytes = need;
+    }
+  }
+  return map_err(launch_backward(reinterpret_cast<const float4 *>(pts), n, g_sdf,
+                                 reinterpret_cast<const float4 *>(g_grad), ctx->bwd_partial, grid,
+                                 reinterpret_cast<float4 *>(g_pts), g_weights, ctx->nets[0],
+                                 a.width, a.n_hidden, a.skip_layer, a.beta, woff, boff, out,
+                                 n_params, s));
 }
 
 nsdf_status nsdf_sync_status(nsdf_ctx *ctx, nsdf_stream stream) {

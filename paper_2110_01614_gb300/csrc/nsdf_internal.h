@@ -65,6 +65,9 @@ struct QueryParams {
   // (fault injection for tests of the timeout path; -1 in normal use)
   long long wait_budget;
   int drop_load;
+  // first-order backward through the query kernel: out_grad[i] = grad_scale[i] * grad f
+  const float *grad_scale;   // nullable
+  float4 *out_grad;
 };
 
 // Launchers (return a cudaError_t from the launch).
@@ -79,5 +82,14 @@ cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bo
                                   int num_sms, cudaStream_t s);
 size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid);
 int query_tc16_grid(int width, int64_t n, int num_sms);
+
+size_t backward_smem_bytes(int width, int n_hidden, int64_t n_params);
+bool backward_supported(int width, int n_hidden, int64_t n_params);
+int backward_grid(int64_t n, int num_sms);
+cudaError_t launch_backward(const float4 *pts, int64_t n, const float *a, const float4 *v,
+                            float *g_partial, int grid, float4 *g_pts, float *g_weights,
+                            const NetDevice &net, int width, int n_hidden, int skip, float beta,
+                            const int64_t *woff, const int64_t *boff, const int *out,
+                            int64_t n_params, cudaStream_t s);
 
 }  // namespace nsdf

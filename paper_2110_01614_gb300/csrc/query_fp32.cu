@@ -308,7 +308,10 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
         const float nrm = sqrtf(gx * gx + gy * gy + gz * gz);
         float nx = 0.f, ny = 0.f, nz = 0.f;
         if (nrm >= 1e-20f) { nx = gx / nrm; ny = gy / nrm; nz = gz / nrm; }
-        if (!prm.collide) {
+        if (prm.grad_scale) {
+          const float a = prm.grad_scale[idx];
+          prm.out_grad[idx] = make_float4(a * gx, a * gy, a * gz, 0.f);
+        } else if (!prm.collide) {
           if (prm.raw_gradient) { nx = gx; ny = gy; nz = gz; }
           prm.out_n_sdf[idx] = make_float4(nx, ny, nz, f);
         } else {

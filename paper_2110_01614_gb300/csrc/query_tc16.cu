@@ -172,9 +172,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// Issue a load of 32 consecutive FP32 columns of this thread's TMEM lane; the
+// registers are valid only after tmem_wait_ld() on the same array.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
       "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
@@ -184,11 +184,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
-
+// Wait for every outstanding TMEM load of this thread.  The registers of `r`
+// are tied to the wait so the compiler cannot read them before it.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
 
 // Store 32 16-bit values (16 packed words) of row r, columns k0..k0+31, into
 // the 128-byte-swizzled K-major activation tile.
@@ -204,19 +213,251 @@ __device__ __forceinline__ void store_a_chunk(uint8_t *A, int r, int k0, const u
   }
 }
 
-// softplus_beta and sigmoid(beta z) from one exponential (fast forms: the
-// value is rounded to 16 bits next, the slope feeds a 16-bit operand).
-__device__ __forceinline__ void act(float z, float beta, float inv_beta, float &h, float &s) {
-  const float e = __expf(-beta * fabsf(z));
-  const float one_e = 1.0f + e;
-  h = fmaxf(z, 0.0f) + __logf(one_e) * inv_beta;
-  const float r = __fdividef(1.0f, one_e);
-  s = (z >= 0.0f) ? r : e * r;
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;\n" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;\n" : "=f"(y) : "f"(x));
+  return y;
 }
 
-struct Roles {
-  int warp, lane;
+// softplus_beta(z) and its slope sigmoid(beta z) from u = exp(-beta |z|):
+//   softplus_beta(z) = max(z, 0) + log1p(u) / beta,
+//   sigmoid(beta z)  = 1 / (1 + u) for z >= 0, u / (1 + u) otherwise.
+// log1p(u) = u * P(u), P the degree-5 Chebyshev interpolant of log1p(u)/u on
+// [0, 1] printed by gen_log1p_poly.py (relative error < 1e-5).  Two MUFU
+// operations (ex2, rcp) per element; the rest runs on the FMA pipe.
+// neg_bl2e = -beta * log2(e).
+__device__ __forceinline__ void act(float z, float neg_bl2e, float inv_beta, float &h, float &s) {
+  const float u = ex2_approx(fabsf(z) * neg_bl2e);
+  float p = -2.344365580e-02f;
+  p = fmaf(p, u, 1.001397327e-01f);
+  p = fmaf(p, u, -2.090795360e-01f);
+  p = fmaf(p, u, 3.248495807e-01f);
+  p = fmaf(p, u, -4.993146523e-01f);
+  p = fmaf(p, u, 9.999905920e-01f);
+  h = fmaf(u * p, inv_beta, fmaxf(z, 0.0f));
+  const float r = rcp_approx(1.0f + u);
+  s = (z >= 0.0f) ? r : u * r;
+}
+
+__device__ __forceinline__ float4 ldg4(const float *p) {
+  return __ldg(reinterpret_cast<const float4 *>(p));
+}
+__device__ __forceinline__ float comp(const float4 &v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ uint32_t comp_u(const uint4 &v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Running sums of an epilogue thread: grad f (partial) and f (partial).
+struct Acc {
+  float gx = 0.f, gy = 0.f, gz = 0.f, f = 0.f;
 };
+
+// Per-thread state of an epilogue thread for one tile.
+struct Epi {
+  uint8_t *A;
+  uint8_t *slab;        // this CTA's slope slab
+  uint32_t t_row;       // TMEM address of lane 32*q, column 0
+  int r, ch;            // tile row (= TMEM lane) and column half
+  float neg_bl2e, inv_beta;
+  float px, py, pz;     // query point in the body frame
+  const float *bias;    // [n_hidden][W]
+  const float *wout;    // [W]
+  const float *w0;      // [W][3]
+  const float *wsk;     // three rows of W: W_s[:, nshort + j]
+  // slope chunk j (8 values, 16 B) of layer l for this row / half
+  __device__ __forceinline__ uint4 *slope(int l, int j) const {
+    return reinterpret_cast<uint4 *>(slab + ((((size_t)l * 2 + ch) * 32 + j) * kM + r) * 16);
+  }
+};
+
+constexpr int kNShort = kW - 3;
+
+// One 32-column chunk of a forward epilogue (layers 1 .. L-1).
+template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP>
+__device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uint32_t (&raw)[32],
+                                          Acc &acc) {
+  const float *b = e.bias + (size_t)l * kW + c0;
+  uint32_t hw[16], sw[16];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 bq = ldg4(b + 4 * q);
+    float4 wq = make_float4(0.f, 0.f, 0.f, 0.f), s0, s1, s2;
+    if (LAST) wq = ldg4(e.wout + c0 + 4 * q);
+    if (AT_SKIP) {
+      s0 = ldg4(e.wsk + c0 + 4 * q);
+      s1 = ldg4(e.wsk + kW + c0 + 4 * q);
+      s2 = ldg4(e.wsk + 2 * kW + c0 + 4 * q);
+    }
+    float hv[4], sv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * q + u;
+      const int c = c0 + i;
+      float z = __uint_as_float(raw[i]) + comp(bq, u);
+      if (AT_SKIP)    // the skip input columns p / sqrt(2), in FP32
+        z = fmaf(kInvSqrt2, fmaf(comp(s0, u), e.px, fmaf(comp(s1, u), e.py, comp(s2, u) * e.pz)), z);
+      act(z, e.neg_bl2e, e.inv_beta, hv[u], sv[u]);
+      if (LAST) {
+        const float wo = comp(wq, u);
+        acc.f = fmaf(wo, hv[u], acc.f);
+        hv[u] = sv[u] * wo;                        // delta_{L-1}
+        if (AT_SKIP) {                             // delta_s feeds the direct term
+          acc.gx = fmaf(hv[u], comp(s0, u) * kInvSqrt2, acc.gx);
+          acc.gy = fmaf(hv[u], comp(s1, u) * kInvSqrt2, acc.gy);
+          acc.gz = fmaf(hv[u], comp(s2, u) * kInvSqrt2, acc.gz);
+        }
+      } else if (FEEDS_SKIP) {
+        hv[u] = (c < kNShort) ? hv[u] * kInvSqrt2 : 0.0f;
+      }
+    }
+    hw[2 * q] = Op<kF16>::pack(hv[0], hv[1]);
+    hw[2 * q + 1] = Op<kF16>::pack(hv[2], hv[3]);
+    sw[2 * q] = Op<kF16>::pack(sv[0], sv[1]);
+    sw[2 * q + 1] = Op<kF16>::pack(sv[2], sv[3]);
+  }
+  store_a_chunk(e.A, e.r, c0, hw);
+  if (!LAST) {
+    const int j0 = (c0 - 256 * e.ch) >> 3;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      *e.slope(l, j0 + t) = make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]);
+  }
+}
+
+// A forward epilogue over the thread's 256 columns, TMEM loads double-buffered.
+template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP>
+__device__ __forceinline__ void fwd_layer(const Epi &e, int l, Acc &acc) {
+  uint32_t ra[32], rb[32];
+  const int cbase = 256 * e.ch;
+  tmem_ld32_async(e.t_row + cbase, ra);
+#pragma unroll 1
+  for (int cc = 0; cc < 8; cc += 2) {
+    tmem_wait_ld(ra);
+    tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
+    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * cc, ra, acc);
+    tmem_wait_ld(rb);
+    if (cc + 2 < 8) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
+    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * (cc + 1), rb, acc);
+  }
+}
+
+// L0 (K = 3) on CUDA cores: no TMEM, same epilogue.
+template <bool kF16, bool FEEDS_SKIP>
+__device__ __forceinline__ void layer0(const Epi &e) {
+#pragma unroll 1
+  for (int cc = 0; cc < 8; ++cc) {
+    const int c0 = 256 * e.ch + 32 * cc;
+    uint32_t hw[16], sw[16];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 bq = ldg4(e.bias + c0 + 4 * q);
+      const float4 w_a = ldg4(e.w0 + 3 * (c0 + 4 * q));       // 12 weights of 4 columns
+      const float4 w_b = ldg4(e.w0 + 3 * (c0 + 4 * q) + 4);
+      const float4 w_c = ldg4(e.w0 + 3 * (c0 + 4 * q) + 8);
+      const float w[12] = {w_a.x, w_a.y, w_a.z, w_a.w, w_b.x, w_b.y,
+                           w_b.z, w_b.w, w_c.x, w_c.y, w_c.z, w_c.w};
+      float hv[4], sv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 4 * q + u;
+        const float z = fmaf(w[3 * u], e.px, fmaf(w[3 * u + 1], e.py, fmaf(w[3 * u + 2], e.pz, comp(bq, u))));
+        act(z, e.neg_bl2e, e.inv_beta, hv[u], sv[u]);
+        if (FEEDS_SKIP) hv[u] = (c < kNShort) ? hv[u] * kInvSqrt2 : 0.0f;
+      }
+      hw[2 * q] = Op<kF16>::pack(hv[0], hv[1]);
+      hw[2 * q + 1] = Op<kF16>::pack(hv[2], hv[3]);
+      sw[2 * q] = Op<kF16>::pack(sv[0], sv[1]);
+      sw[2 * q + 1] = Op<kF16>::pack(sv[2], sv[3]);
+    }
+    store_a_chunk(e.A, e.r, c0, hw);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      *e.slope(0, 4 * cc + t) = make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]);
+  }
+}
+
+// One 32-column chunk of a reverse epilogue: delta_{l-1} = slope_{l-1} * g.
+template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT>
+__device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (&raw)[32],
+                                          const uint4 (&sl)[4], Acc &acc) {
+  uint32_t dw[16];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float4 s0, s1, s2, w_a, w_b, w_c;
+    if (MAKES_SKIP_DELTA) {
+      s0 = ldg4(e.wsk + c0 + 4 * q);
+      s1 = ldg4(e.wsk + kW + c0 + 4 * q);
+      s2 = ldg4(e.wsk + 2 * kW + c0 + 4 * q);
+    }
+    if (TO_INPUT) {
+      w_a = ldg4(e.w0 + 3 * (c0 + 4 * q));
+      w_b = ldg4(e.w0 + 3 * (c0 + 4 * q) + 4);
+      w_c = ldg4(e.w0 + 3 * (c0 + 4 * q) + 8);
+    }
+    const uint32_t swords[2] = {comp_u(sl[q >> 1], 2 * (q & 1)), comp_u(sl[q >> 1], 2 * (q & 1) + 1)};
+    const float2 sa = Op<kF16>::unpack(swords[0]);
+    const float2 sb = Op<kF16>::unpack(swords[1]);
+    const float sv[4] = {sa.x, sa.y, sb.x, sb.y};
+    float dv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * q + u;
+      const int c = c0 + i;
+      float g = __uint_as_float(raw[i]);
+      if (AT_SKIP) g = (c < kNShort) ? g * kInvSqrt2 : 0.0f;
+      dv[u] = sv[u] * g;
+      if (MAKES_SKIP_DELTA) {                      // direct path to the input
+        acc.gx = fmaf(dv[u], comp(s0, u) * kInvSqrt2, acc.gx);
+        acc.gy = fmaf(dv[u], comp(s1, u) * kInvSqrt2, acc.gy);
+        acc.gz = fmaf(dv[u], comp(s2, u) * kInvSqrt2, acc.gz);
+      }
+      if (TO_INPUT) {
+        const float w[12] = {w_a.x, w_a.y, w_a.z, w_a.w, w_b.x, w_b.y,
+                             w_b.z, w_b.w, w_c.x, w_c.y, w_c.z, w_c.w};
+        acc.gx = fmaf(dv[u], w[3 * u], acc.gx);
+        acc.gy = fmaf(dv[u], w[3 * u + 1], acc.gy);
+        acc.gz = fmaf(dv[u], w[3 * u + 2], acc.gz);
+      }
+    }
+    dw[2 * q] = Op<kF16>::pack(dv[0], dv[1]);
+    dw[2 * q + 1] = Op<kF16>::pack(dv[2], dv[3]);
+  }
+  if (!TO_INPUT) store_a_chunk(e.A, e.r, c0, dw);
+}
+
+// A reverse epilogue over the thread's 256 columns: TMEM loads and the
+// slopes of the next chunk are fetched while the current chunk is processed.
+template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT>
+__device__ __forceinline__ void bwd_layer(const Epi &e, int l, Acc &acc) {
+  uint32_t ra[32], rb[32];
+  uint4 sa[4], sb[4];
+  const int cbase = 256 * e.ch;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) sa[t] = *e.slope(l - 1, t);
+  tmem_ld32_async(e.t_row + cbase, ra);
+#pragma unroll 1
+  for (int cc = 0; cc < 8; cc += 2) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) sb[t] = *e.slope(l - 1, 4 * (cc + 1) + t);
+    tmem_wait_ld(ra);
+    tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
+    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * cc, ra, sa, acc);
+    if (cc + 2 < 8) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) sa[t] = *e.slope(l - 1, 4 * (cc + 2) + t);
+    }
+    tmem_wait_ld(rb);
+    if (cc + 2 < 8) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
+    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * (cc + 1), rb, sb, acc);
+  }
+}
 
 template <bool kF16>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -283,9 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t issued_parity[kStages];
-      bool issued[kStages];
-      for (int s = 0; s < kStages; ++s) issued[s] = false, issued_parity[s] = 0;
+      uint32_t issued_mask = 0, issued_parity = 0;   // per stage: a load in flight, its phase
       int64_t load_idx = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
@@ -305,8 +544,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               mbar_expect_tx(full_bar(stage), kStageBytes);
               tma_load_2d(sB + stage * kStageBytes, map, kb * kKAtom, rowbase + nh * kN,
                           full_bar(stage));
-              issued[stage] = true;
-              issued_parity[stage] = phase;
+              issued_mask |= 1u << stage;
+              issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
             }
             if (++stage == kStages) stage = 0, phase ^= 1u;
           }
@@ -314,9 +553,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // drain: every issued load must land before the CTA may exit
       for (int s = 0; s < kStages; ++s) {
-        if (issued[s]) {
+        if (issued_mask & (1u << s)) {
           volatile int no_abort = 0;
-          if (!mbar_wait(full_bar(s), issued_parity[s], budget, &no_abort)) fail();
+          if (!mbar_wait(full_bar(s), (issued_parity >> s) & 1u, budget, &no_abort)) fail();
         }
       }
     }
@@ -364,22 +603,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------- epilogue warps ----------------
-    const int e = warp - 2;
     const int q = warp & 3;                  // TMEM lane quarter
-    const int ch = e >> 2;                   // column half
+    const int ch = (warp - 2) >> 2;          // column half
     const int r = 32 * q + lane;             // row of the tile = TMEM lane
-    const uint32_t t_row = tmem + ((uint32_t)(32 * q) << 16);
-    const float beta = prm.beta, inv_beta = 1.0f / prm.beta;
     const int skip = prm.skip;
-    const int nshort = kW - 3;
+    Epi e;
+    e.A = A;
+    e.slab = reinterpret_cast<uint8_t *>(prm.scratch) +
+             (size_t)blockIdx.x * (size_t)(L - 1) * 2 * 32 * kM * 16;
+    e.t_row = tmem + ((uint32_t)(32 * q) << 16);
+    e.r = r;
+    e.ch = ch;
+    e.neg_bl2e = -prm.beta * 1.4426950408889634f;
+    e.inv_beta = 1.0f / prm.beta;
+    e.bias = prm.bias;
+    e.wout = prm.wout;
+    e.w0 = prm.w0;
     // W_s[:, nshort + j] (j = 0..2): the skip layer's weights on p, FP32, from
     // the transposed copy (row k = nshort + j holds W_s[n][k] over n)
-    const float *wsk = skip > 0 ? prm.fwd_t + ((size_t)(skip - 1) * kW + nshort) * kW : prm.fwd_t;
-    uint8_t *slab = reinterpret_cast<uint8_t *>(prm.scratch) +
-                    (size_t)blockIdx.x * (size_t)(L - 1) * 2 * 32 * kM * 16;
-    auto slab_chunk = [&](int l, int j) -> uint4 * {   // 8 slopes (16 B) of row r
-      return reinterpret_cast<uint4 *>(slab + ((((size_t)l * 2 + ch) * 32 + j) * kM + r) * 16);
-    };
+    e.wsk = skip > 0 ? prm.fwd_t + ((size_t)(skip - 1) * kW + kNShort) * kW : prm.fwd_t;
     uint32_t d_phase = 0, x_phase = 0;
     bool ok = true;
     auto arrive_a = [&]() {
@@ -392,91 +634,35 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t idx = tile * kM + r;
       float4 pw = make_float4(0.f, 0.f, 0.f, 0.f);
       if (idx < prm.n) pw = prm.pts[idx];
-      float px = pw.x, py = pw.y, pz = pw.z;
+      e.px = pw.x; e.py = pw.y; e.pz = pw.z;
       if (prm.has_T) {
         const float *t = prm.Ti;
-        px = t[0] * pw.x + t[1] * pw.y + t[2] * pw.z + t[3];
-        py = t[4] * pw.x + t[5] * pw.y + t[6] * pw.z + t[7];
-        pz = t[8] * pw.x + t[9] * pw.y + t[10] * pw.z + t[11];
+        e.px = t[0] * pw.x + t[1] * pw.y + t[2] * pw.z + t[3];
+        e.py = t[4] * pw.x + t[5] * pw.y + t[6] * pw.z + t[7];
+        e.pz = t[8] * pw.x + t[9] * pw.y + t[10] * pw.z + t[11];
       }
-      float fpart = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+      Acc acc;
 
       // ---- L0 on CUDA cores ----
-      {
-        const bool feeds_skip = (skip == 1);
-        for (int cc = 0; cc < 8; ++cc) {
-          const int c0 = ch * 256 + cc * 32;
-          uint32_t hw[16], sw[16];
-#pragma unroll
-          for (int i = 0; i < 32; i += 2) {
-            float hv[2], sv[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int c = c0 + i + u;
-              const float z = fmaf(prm.w0[3 * c], px, fmaf(prm.w0[3 * c + 1], py,
-                                   fmaf(prm.w0[3 * c + 2], pz, prm.bias[c])));
-              act(z, beta, inv_beta, hv[u], sv[u]);
-              if (feeds_skip) hv[u] = (c < nshort) ? hv[u] * kInvSqrt2 : 0.0f;
-            }
-            hw[i / 2] = Op<kF16>::pack(hv[0], hv[1]);
-            sw[i / 2] = Op<kF16>::pack(sv[0], sv[1]);
-          }
-          store_a_chunk(A, r, c0, hw);
-#pragma unroll
-          for (int t = 0; t < 4; ++t)
-            *slab_chunk(0, cc * 4 + t) = make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]);
-        }
-        arrive_a();
-      }
+      if (skip == 1) layer0<kF16, true>(e);
+      else layer0<kF16, false>(e);
+      arrive_a();
 
       // ---- hidden layers L1 .. L{L-1} (forward) ----
       for (int l = 1; ok && l < L; ++l) {
         if (!mbar_wait(d_full, d_phase, budget, abort_flag)) { fail(); ok = false; break; }
         d_phase ^= 1u;
         tc_fence_after();
-        const bool last = (l == L - 1);
-        const bool feeds_skip = (skip > 0 && l == skip - 1);
-        const bool at_skip = (skip > 0 && l == skip);
-        const float *b = prm.bias + (size_t)l * kW;
-        for (int cc = 0; cc < 8; ++cc) {
-          const int c0 = ch * 256 + cc * 32;
-          float v[32];
-          tmem_ld32(t_row + (uint32_t)c0, v);
-          uint32_t hw[16], sw[16];
-#pragma unroll
-          for (int i = 0; i < 32; i += 2) {
-            float hv[2], sv[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int c = c0 + i + u;
-              float z = v[i + u] + __ldg(b + c);
-              if (at_skip) {   // the input columns p / sqrt(2), in FP32
-                z = fmaf(kInvSqrt2, fmaf(__ldg(wsk + c), px, fmaf(__ldg(wsk + kW + c), py,
-                                         __ldg(wsk + 2 * kW + c) * pz)), z);
-              }
-              act(z, beta, inv_beta, hv[u], sv[u]);
-              if (last) {
-                const float wo = __ldg(prm.wout + c);
-                fpart = fmaf(wo, hv[u], fpart);
-                hv[u] = sv[u] * wo;                     // delta_{L-1}
-                if (skip == L - 1) {                     // delta_s feeds the direct term
-                  gx = fmaf(hv[u], __ldg(wsk + c) * kInvSqrt2, gx);
-                  gy = fmaf(hv[u], __ldg(wsk + kW + c) * kInvSqrt2, gy);
-                  gz = fmaf(hv[u], __ldg(wsk + 2 * kW + c) * kInvSqrt2, gz);
-                }
-              } else if (feeds_skip) {
-                hv[u] = (c < nshort) ? hv[u] * kInvSqrt2 : 0.0f;
-              }
-            }
-            hw[i / 2] = Op<kF16>::pack(hv[0], hv[1]);
-            sw[i / 2] = Op<kF16>::pack(sv[0], sv[1]);
-          }
-          store_a_chunk(A, r, c0, hw);
-          if (!last) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-              *slab_chunk(l, cc * 4 + t) = make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]);
-          }
+        const bool last = (l == L - 1), at = (l == skip), feeds = (l == skip - 1);
+        if (last) {
+          if (at) fwd_layer<kF16, true, true, false>(e, l, acc);
+          else fwd_layer<kF16, true, false, false>(e, l, acc);
+        } else if (at) {
+          fwd_layer<kF16, false, true, false>(e, l, acc);
+        } else if (feeds) {
+          fwd_layer<kF16, false, false, true>(e, l, acc);
+        } else {
+          fwd_layer<kF16, false, false, false>(e, l, acc);
         }
         arrive_a();
       }
@@ -486,49 +672,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(d_full, d_phase, budget, abort_flag)) { fail(); ok = false; break; }
         d_phase ^= 1u;
         tc_fence_after();
-        const bool at_skip = (skip > 0 && l == skip);
-        const bool makes_skip_delta = (skip > 0 && l - 1 == skip);
-        const bool to_input = (l == 1);
-        for (int cc = 0; cc < 8; ++cc) {
-          const int c0 = ch * 256 + cc * 32;
-          float v[32];
-          tmem_ld32(t_row + (uint32_t)c0, v);
-          uint32_t sw[16];
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const uint4 s4 = *slab_chunk(l - 1, cc * 4 + t);
-            sw[4 * t] = s4.x; sw[4 * t + 1] = s4.y; sw[4 * t + 2] = s4.z; sw[4 * t + 3] = s4.w;
-          }
-          uint32_t dw[16];
-#pragma unroll
-          for (int i = 0; i < 32; i += 2) {
-            const float2 s2 = Op<kF16>::unpack(sw[i / 2]);
-            float dv[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int c = c0 + i + u;
-              float g = v[i + u];
-              if (at_skip) g = (c < nshort) ? g * kInvSqrt2 : 0.0f;
-              dv[u] = (u == 0 ? s2.x : s2.y) * g;
-              if (makes_skip_delta) {                   // direct path to the input
-                gx = fmaf(dv[u], __ldg(wsk + c) * kInvSqrt2, gx);
-                gy = fmaf(dv[u], __ldg(wsk + kW + c) * kInvSqrt2, gy);
-                gz = fmaf(dv[u], __ldg(wsk + 2 * kW + c) * kInvSqrt2, gz);
-              }
-              if (to_input) {
-                gx = fmaf(dv[u], __ldg(prm.w0 + 3 * c), gx);
-                gy = fmaf(dv[u], __ldg(prm.w0 + 3 * c + 1), gy);
-                gz = fmaf(dv[u], __ldg(prm.w0 + 3 * c + 2), gz);
-              }
-            }
-            dw[i / 2] = Op<kF16>::pack(dv[0], dv[1]);
-          }
-          if (!to_input) store_a_chunk(A, r, c0, dw);
+        const bool at = (l == skip), makes = (l - 1 == skip), to_input = (l == 1);
+        if (to_input) {
+          if (at) bwd_layer<kF16, true, false, true>(e, l, acc);
+          else bwd_layer<kF16, false, false, true>(e, l, acc);
+          tc_fence_before();
+        } else {
+          if (at) bwd_layer<kF16, true, false, false>(e, l, acc);
+          else if (makes) bwd_layer<kF16, false, true, false>(e, l, acc);
+          else bwd_layer<kF16, false, false, false>(e, l, acc);
+          arrive_a();
         }
-        if (!to_input) arrive_a();
-        else tc_fence_before();
       }
       if (!ok) break;
+      float gx = acc.gx, gy = acc.gy, gz = acc.gz, fpart = acc.f;
 
       // ---- a7-a9: combine the two column halves, normalise, test, project ----
       if (ch == 1) {
