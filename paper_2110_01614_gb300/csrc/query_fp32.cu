@@ -354,6 +354,11 @@ template <int W>
 int grid_w(int64_t n, int num_sms) {
   using C = Cfg<W>;
   int per_sm = 1;
+  // The occupancy of a kernel above 48 KB of dynamic shared memory is only
+  // known once its opt-in attribute is set; set it before asking, so that the
+  // grid used to size the scratch equals the grid that is launched.
+  cudaFuncSetAttribute(query_fp32_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)C::SMEM_BYTES);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, query_fp32_kernel<W>, kThreads,
                                                 C::SMEM_BYTES);
   if (per_sm < 1) per_sm = 1;

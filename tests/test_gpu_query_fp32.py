@@ -206,3 +206,24 @@ def test_full_size_sampled_parity(nsdf):
     f, N, hit, x = mlp.collide(blob, BODY, pts[idx], 0.002)
     check_collide(f, N, hit, x, 0.002, out_pts.cpu().numpy()[idx], out_ns.cpu().numpy()[idx],
                   out_hit.cpu().numpy()[idx], pts[idx])
+
+
+def test_first_call_in_fresh_process_with_many_tiles():
+    """The first launch of a process (kernel attributes not yet set) must size
+    its scratch for the grid it launches: 3,126 tiles of the tiny network."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import torch, synth, paper_2110_01614_gb300 as nsdf\n"
+        "a = synth.Arch(3, 64, 3, -1, 100.0)\n"
+        "s = nsdf.NeuralSDF(a, nsdf.NSDF_FP32).load(synth.geometric_init(a, 0))\n"
+        "p = torch.from_numpy(synth.body_scale_points(200001, 11)).cuda()\n"
+        "o = s.collide(p, 0.002)\n"
+        "nsdf.nsdf_sync_status(s.ctx)\n"
+        "torch.cuda.synchronize()\n"
+        "print('ok')\n" % root)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
