@@ -51,7 +51,8 @@ typedef enum {
   NSDF_ERR_OOM = 4,          /* device allocation failed                     */
   NSDF_ERR_CUDA = 5,         /* a CUDA runtime call failed                   */
   NSDF_ERR_UNSUPPORTED = 6,  /* shape / precision this build has no kernel for */
-  NSDF_ERR_TIMEOUT = 7       /* a bounded wait inside a kernel ran out        */
+  NSDF_ERR_TIMEOUT = 7,      /* a bounded wait inside a kernel ran out        */
+  NSDF_ERR_TOO_LARGE = 8     /* exceeds the fixed scratch of nsdf_collide_noalloc */
 } nsdf_status;
 
 typedef enum {
@@ -132,6 +133,30 @@ nsdf_status nsdf_query(nsdf_ctx *ctx, const float *pts, int64_t n,
 nsdf_status nsdf_collide(nsdf_ctx *ctx, const float *pts, int64_t n, float eps,
                          const float *T, float *out_pts, float *out_n_sdf,
                          uint8_t *out_hit, nsdf_stream stream);
+
+/*
+ * nsdf_collide without any allocation, for callers that cannot allocate
+ * device memory when they query: a simulator running inside a fixed memory
+ * budget, code that records its GPU work into a CUDA graph or calls from a
+ * real-time callback (where cudaMalloc would synchronise or is forbidden),
+ * or a host that forbids the library from growing after set-up.  The paper
+ * has no counterpart; this is a property of the library, not of the method.
+ *
+ * Same arguments and results as nsdf_collide (device pointers only).  The
+ * kernels' scratch comes from one fixed 32 MiB device array that every GPU
+ * loading the library holds until exit; the launch uses as many CTAs as
+ * whole per-CTA scratch slabs fit in it, so wide networks run on fewer SMs.
+ * A network whose scratch for one CTA exceeds the array is rejected with
+ * NSDF_ERR_TOO_LARGE.  No cudaMalloc, cudaFree or allocating library call is
+ * made.  The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls share the array: calls that may overlap on the GPU (other streams,
+ * other threads) race on it and must be serialised by the caller.
+ */
+nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int64_t n,
+                                 float eps, const float *T, float *out_pts,
+                                 float *out_n_sdf, uint8_t *out_hit,
+                                 nsdf_stream stream);
 
 /*
  * Gradients of L = sum_i g_sdf[i] f(p_i) + g_grad[i] . grad f(p_i) for

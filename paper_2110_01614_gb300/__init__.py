@@ -22,7 +22,7 @@ from ._abi import (NSDF_BF16, NSDF_FP16, NSDF_FP32, NSDF_RAW_GRADIENT, nsdf_arch
 __all__ = [
     "NsdfError", "NSDF_FP32", "NSDF_BF16", "NSDF_FP16", "NSDF_RAW_GRADIENT", "make_arch",
     "nsdf_num_params", "nsdf_create", "nsdf_destroy", "nsdf_load_weights",
-    "nsdf_query", "nsdf_collide", "nsdf_backward", "nsdf_query_grouped",
+    "nsdf_query", "nsdf_collide", "nsdf_collide_noalloc", "nsdf_backward", "nsdf_query_grouped",
     "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status", "nsdf_debug_inject",
     "nsdf_status_string", "NeuralSDF", "library",
 ]
@@ -117,6 +117,17 @@ def nsdf_collide(ctx, pts, eps, out_pts, out_n_sdf=None, out_hit=None, T=None, s
                                   ctypes.cast(Tc, ctypes.c_void_p) if Tc is not None else None,
                                   _ptr(out_pts), _ptr(out_n_sdf), _ptr(out_hit),
                                   _stream(stream)), "nsdf_collide")
+
+
+def nsdf_collide_noalloc(ctx, pts, eps, out_pts, out_n_sdf=None, out_hit=None, T=None,
+                         stream=None):
+    """nsdf_collide with no allocation: scratch from the library's fixed device array."""
+    Tc = _transform(T)
+    _check(library().nsdf_collide_noalloc(ctx, _ptr(pts), pts.shape[0], float(eps),
+                                          ctypes.cast(Tc, ctypes.c_void_p) if Tc is not None
+                                          else None, _ptr(out_pts), _ptr(out_n_sdf),
+                                          _ptr(out_hit), _stream(stream)),
+           "nsdf_collide_noalloc")
 
 
 def nsdf_backward(ctx, pts, g_sdf, g_grad=None, g_weights=None, g_pts=None, stream=None):

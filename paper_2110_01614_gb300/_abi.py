@@ -19,6 +19,7 @@ NSDF_ERR_OOM = 4
 NSDF_ERR_CUDA = 5
 NSDF_ERR_UNSUPPORTED = 6
 NSDF_ERR_TIMEOUT = 7
+NSDF_ERR_TOO_LARGE = 8
 
 NSDF_FP32 = 0
 NSDF_BF16 = 1
@@ -45,6 +46,7 @@ SIGNATURES = {
     "nsdf_load_weights": (_ST, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int, _P]),
     "nsdf_query": (_ST, [_P, _P, _I64, _P, ctypes.c_uint32, _P]),
     "nsdf_collide": (_ST, [_P, _P, _I64, ctypes.c_float, _P, _P, _P, _P, _P]),
+    "nsdf_collide_noalloc": (_ST, [_P, _P, _I64, ctypes.c_float, _P, _P, _P, _P, _P]),
     "nsdf_backward": (_ST, [_P, _P, _I64, _P, _P, _P, _P, _P]),
     "nsdf_query_grouped": (_ST, [_P, _P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]),
     "nsdf_mesh_sdf": (_ST, [_P, _I64, _P, _I64, _P, _I64, _P, _P]),

@@ -330,6 +330,25 @@ nsdf_status collide_host(nsdf_ctx *ctx, QueryParams base, const float *pts, int6
 
 }  // namespace
 
+namespace nsdf {
+
+nsdf_status ctx_query_setup(nsdf_ctx *ctx, QueryParams *p, int *num_sms, int *width,
+                            int *n_hidden, bool *tc16, bool *fp16, const NetDevice **net) {
+  if (!ctx->nets[0].loaded) return NSDF_ERR_NOT_LOADED;
+  fill_net(ctx, 0, *p);
+  *num_sms = ctx->num_sms;
+  *width = ctx->arch.width;
+  *n_hidden = ctx->arch.n_hidden;
+  *tc16 = use_bf16(ctx);
+  *fp16 = ctx->prec == NSDF_FP16;
+  *net = &ctx->nets[0];
+  return NSDF_OK;
+}
+
+nsdf_status ctx_set_transform(const float *T, QueryParams *p) { return set_transform(T, *p); }
+
+}  // namespace nsdf
+
 extern "C" {
 
 size_t nsdf_num_params(const nsdf_arch *arch) {
@@ -350,6 +369,7 @@ const char *nsdf_status_string(nsdf_status s) {
     case NSDF_ERR_CUDA: return "CUDA runtime error";
     case NSDF_ERR_UNSUPPORTED: return "unsupported shape or precision";
     case NSDF_ERR_TIMEOUT: return "bounded wait in a kernel ran out";
+    case NSDF_ERR_TOO_LARGE: return "request exceeds the fixed scratch of the allocation-free entry point";
   }
   return "unknown status";
 }

@@ -83,6 +83,12 @@ cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bo
 size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid);
 int query_tc16_grid(int width, int64_t n, int num_sms);
 
+// Context accessors for entry points defined outside api.cu: the network-0
+// launch parameters of a loaded context, and the transform of nsdf_collide.
+nsdf_status ctx_query_setup(nsdf_ctx *ctx, QueryParams *p, int *num_sms, int *width,
+                            int *n_hidden, bool *tc16, bool *fp16, const NetDevice **net);
+nsdf_status ctx_set_transform(const float *T, QueryParams *p);
+
 size_t backward_smem_bytes(int width, int n_hidden, int64_t n_params);
 bool backward_supported(int width, int n_hidden, int64_t n_params);
 int backward_grid(int64_t n, int num_sms);
