@@ -244,6 +244,26 @@ __device__ __forceinline__ void act(float z, float neg_bl2e, float inv_beta, flo
   s = (z >= 0.0f) ? r : u * r;
 }
 
+// Slopes are written once and read once, one tile-time later.  They are
+// stored with an L2 evict-last policy, and each 128-byte line is discarded
+// from L2 after its single read, so dead slopes are never written back to HBM.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void st_slope(uint4 *dst, uint4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(dst),
+               "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void l2_discard_line(const void *line) {
+  asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(line) : "memory");
+}
+__device__ __forceinline__ void l2_prefetch_bulk(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ float4 ldg4(const float *p) {
   return __ldg(reinterpret_cast<const float4 *>(p));
 }
@@ -271,6 +291,8 @@ struct Epi {
   const float *wout;    // [W]
   const float *w0;      // [W][3]
   const float *wsk;     // three rows of W: W_s[:, nshort + j]
+  uint64_t pol;         // L2 evict-last policy for slope stores
+  int lane;
   // slope chunk j (8 values, 16 B) of layer l for this row / half
   __device__ __forceinline__ uint4 *slope(int l, int j) const {
     return reinterpret_cast<uint4 *>(slab + ((((size_t)l * 2 + ch) * 32 + j) * kM + r) * 16);
@@ -327,7 +349,8 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
     const int j0 = (c0 - 256 * e.ch) >> 3;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      *e.slope(l, j0 + t) = make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]);
+      st_slope(e.slope(l, j0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
+               e.pol);
   }
 }
 
@@ -379,7 +402,8 @@ __device__ __forceinline__ void layer0(const Epi &e) {
     store_a_chunk(e.A, e.r, c0, hw);
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      *e.slope(0, 4 * cc + t) = make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]);
+      st_slope(e.slope(0, 4 * cc + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
+               e.pol);
   }
 }
 
@@ -432,6 +456,18 @@ __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (
   if (!TO_INPUT) store_a_chunk(e.A, e.r, c0, dw);
 }
 
+// After a chunk's slopes have been consumed, drop their L2 lines: the warp's
+// 32 rows x 4 slope groups cover 16 lines of 128 bytes, one per lane 0..15.
+__device__ __forceinline__ void discard_chunk(const Epi &e, int l, int cc) {
+  __syncwarp();
+  if (e.lane < 16) {
+    const int j = 4 * cc + (e.lane >> 2);
+    const int row0 = (e.r & ~31) + 8 * (e.lane & 3);
+    const uint8_t *line = e.slab + ((((size_t)l * 2 + e.ch) * 32 + j) * kM + row0) * 16;
+    l2_discard_line(line);
+  }
+}
+
 // A reverse epilogue over the thread's 256 columns: TMEM loads and the
 // slopes of the next chunk are fetched while the current chunk is processed.
 template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT>
@@ -449,6 +485,7 @@ __device__ __forceinline__ void bwd_layer(const Epi &e, int l, Acc &acc) {
     tmem_wait_ld(ra);
     tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
     bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * cc, ra, sa, acc);
+    discard_chunk(e, l - 1, cc);
     if (cc + 2 < 8) {
 #pragma unroll
       for (int t = 0; t < 4; ++t) sa[t] = *e.slope(l - 1, 4 * (cc + 2) + t);
@@ -456,6 +493,7 @@ __device__ __forceinline__ void bwd_layer(const Epi &e, int l, Acc &acc) {
     tmem_wait_ld(rb);
     if (cc + 2 < 8) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
     bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * (cc + 1), rb, sb, acc);
+    discard_chunk(e, l - 1, cc + 1);
   }
 }
 
@@ -622,6 +660,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // W_s[:, nshort + j] (j = 0..2): the skip layer's weights on p, FP32, from
     // the transposed copy (row k = nshort + j holds W_s[n][k] over n)
     e.wsk = skip > 0 ? prm.fwd_t + ((size_t)(skip - 1) * kW + kNShort) * kW : prm.fwd_t;
+    e.pol = l2_evict_last_policy();
+    e.lane = lane;
+    const bool prefetcher = (warp == 2 && lane == 0);
     uint32_t d_phase = 0, x_phase = 0;
     bool ok = true;
     auto arrive_a = [&]() {
@@ -669,6 +710,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
       // ---- Jacobian-transpose chain: layers L-1 .. 1 ----
       for (int l = L - 1; ok && l >= 1; --l) {
+        // bring this layer's slopes (128 KB of this CTA) into L2 while its products run
+        if (prefetcher) l2_prefetch_bulk(e.slab + (size_t)(l - 1) * 2 * 32 * kM * 16, 2 * 32 * kM * 16);
         if (!mbar_wait(d_full, d_phase, budget, abort_flag)) { fail(); ok = false; break; }
         d_phase ^= 1u;
         tc_fence_after();
