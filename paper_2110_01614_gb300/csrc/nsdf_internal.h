@@ -82,6 +82,7 @@ cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bo
                                   int num_sms, cudaStream_t s);
 size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid);
 int query_tc16_grid(int width, int64_t n, int num_sms);
+int query_tc16_min_grid();   // CTAs of one cluster: the smallest grid of the kernel
 
 // Context accessors for entry points defined outside api.cu: the network-0
 // launch parameters of a loaded context, and the transform of nsdf_collide.

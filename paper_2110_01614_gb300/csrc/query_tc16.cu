@@ -43,6 +43,11 @@ constexpr int kM = 128;                    // points per tile (MMA M, TMEM lanes
 constexpr int kN = 256;                    // MMA N (one half of a layer)
 constexpr int kKAtom = 64;                 // K elements per 128-byte swizzle atom
 constexpr int kStages = 3;
+// CTAs per cluster sharing every weight panel: each CTA fetches 1/kCluster of
+// the panel's rows and the TMA multicasts it into all of them, so L2 streams
+// each panel once per cluster instead of once per CTA.
+constexpr int kCluster = 2;
+constexpr int kSliceRows = 256 / kCluster;
 constexpr int kStageBytes = kN * kKAtom * 2;          // 32 KB weight panel
 constexpr int kABytes = kM * kW * 2;                  // 128 KB activation tile
 constexpr int kAtomBytes = kM * kKAtom * 2;           // 16 KB: one K atom of A
@@ -137,6 +142,33 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long 
     if (clock64() - t0 > budget) return false;
   }
   return true;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// Load a box into the same shared-memory offset of every CTA in `mask`,
+// completing the transaction bytes on each CTA's barrier at offset `bar`.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                               uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+      : "memory");
+}
+// Arrive on the barrier at offset `bar` of every CTA in `mask` once this
+// thread's previously issued MMAs have completed.
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;\n" ::"r"(bar), "h"(mask)
+      : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
@@ -530,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
+      mbar_init(empty_bar(s), kCluster);   // freed when every CTA of the cluster consumed it
     }
     mbar_init(a_ready, kEpiWarps);
     mbar_init(d_full, 1);
@@ -549,8 +581,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();      // every CTA's barriers exist before any multicast targets them
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t crank = cluster_rank();
+  const uint16_t cmask = (uint16_t)((1u << kCluster) - 1u);
+  // every CTA walks the same number of tiles (the cluster's CTAs consume the
+  // same weight panels in lockstep); tiles past the end are all-masked
+  const int64_t iters = (ntiles + gridDim.x - 1) / gridDim.x;
 
   auto fail = [&]() {
     atomicExch(prm.err, kDevTimeout);
@@ -565,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued_mask = 0, issued_parity = 0;   // per stage: a load in flight, its phase
       int64_t load_idx = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      for (int64_t it = 0; ok && it < iters; ++it) {
         for (int li = 0; ok && li < G; ++li) {
           const bool fwd = li < L - 1;
           const int l = fwd ? li + 1 : G - li;           // network layer of this product
@@ -579,9 +617,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const int nh = ld / (kW / kKAtom), kb = ld % (kW / kKAtom);
             if (load_idx != prm.drop_load) {
-              mbar_expect_tx(full_bar(stage), kStageBytes);
-              tma_load_2d(sB + stage * kStageBytes, map, kb * kKAtom, rowbase + nh * kN,
-                          full_bar(stage));
+              mbar_expect_tx(full_bar(stage), kStageBytes);   // all slices land here
+              tma_load_2d_mc(sB + stage * kStageBytes + crank * (kSliceRows * kKAtom * 2), map,
+                             kb * kKAtom, rowbase + nh * kN + (int)crank * kSliceRows,
+                             full_bar(stage), cmask);
               issued_mask |= 1u << stage;
               issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
             }
@@ -603,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0, a_phase = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      for (int64_t it = 0; ok && it < iters; ++it) {
         for (int li = 0; ok && li < G; ++li) {
           if (!mbar_wait(a_ready, a_phase, budget, abort_flag)) {
             fail();
@@ -628,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               mma_16(d, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32),
                      Op<kF16>::idesc, (kb | ks) != 0 ? 1u : 0u);
             }
-            mma_commit(empty_bar(stage));
+            mma_commit_mc(empty_bar(stage), cmask);
             if (++stage == kStages) stage = 0, phase ^= 1u;
           }
           if (ok) mma_commit(d_full);
@@ -671,7 +710,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(a_ready);
     };
-    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+    for (int64_t it = 0; ok && it < iters; ++it) {
+      const int64_t tile = blockIdx.x + it * gridDim.x;
       const int64_t idx = tile * kM + r;
       float4 pw = make_float4(0.f, 0.f, 0.f, 0.f);
       if (idx < prm.n) pw = prm.pts[idx];
@@ -777,6 +817,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
+  cluster_sync();      // no CTA leaves while a peer may still multicast into it
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kW));
@@ -801,7 +842,7 @@ bool encode_panel_map(CUtensorMap *map, void *base, int rows, bool fp16) {
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)kW, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kW * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kKAtom, (cuuint32_t)kN};
+  cuuint32_t box[2] = {(cuuint32_t)kKAtom, (cuuint32_t)kSliceRows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -823,11 +864,48 @@ bool make_tc16_tmaps(NetDevice &net, int width, int n_hidden, bool fp16) {
          encode_panel_map(&net.tmap_bwd, net.bwd16, rows, fp16);
 }
 
+// CTAs of this kernel that can be resident at once in whole clusters (a GPC
+// with an odd number of free SMs cannot host a full cluster on all of them).
+static int resident_cluster_ctas(int num_sms) {
+  static int cached[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev] < num_sms ? cached[dev] : num_sms;
+  cudaFuncSetAttribute(query_tc16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCluster * 256, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, query_tc16_kernel<false>, &cfg) != cudaSuccess ||
+      clusters < 1) {
+    cudaGetLastError();
+    clusters = num_sms / kCluster;
+  }
+  const int ctas = clusters * kCluster;
+  if (dev >= 0 && dev < 64) cached[dev] = ctas;
+  return ctas < num_sms ? ctas : num_sms;
+}
+
+int query_tc16_min_grid() { return kCluster; }
+
 int query_tc16_grid(int width, int64_t n, int num_sms) {
   (void)width;
   const int64_t tiles = (n + kM - 1) / kM;
-  return (int)(tiles < num_sms ? (tiles < 1 ? 1 : tiles) : num_sms);
+  const int cap = resident_cluster_ctas(num_sms);
+  int64_t g = tiles < cap ? tiles : cap;
+  g = (g / kCluster) * kCluster;                 // whole clusters
+  return (int)(g < kCluster ? kCluster : g);
 }
+
+
 
 size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid) {
   (void)width;
@@ -840,7 +918,20 @@ cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cu
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   const int grid = query_tc16_grid(p.width, p.n, num_sms);
-  query_tc16_kernel<kF16><<<grid, kThreads, kSmemBytes, s>>>(p, net.tmap_fwd, net.tmap_bwd);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, query_tc16_kernel<kF16>, p, net.tmap_fwd, net.tmap_bwd);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
