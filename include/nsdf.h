@@ -172,16 +172,41 @@ nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n,
 
 /*
  * Many bodies in one launch: network k answers points
- * pts[offsets[k] .. offsets[k] + counts[k]) for k < n_nets of the context.
- * offsets and counts are DEVICE int64 arrays (so a captured CUDA graph can
- * be replayed with new counts); max_total bounds offsets[k] + counts[k] and
- * sizes the work list.  Outputs as nsdf_collide (no transform); out_n_sdf
- * nullable.  Points outside every range are left untouched.
+ * pts[offsets[k] .. offsets[k] + counts[k]) for k < n_nets of the context,
+ * with the collision solve of nsdf_collide (no transform).  offsets and
+ * counts are DEVICE int64 arrays: the work list is built on the device, so a
+ * CUDA graph that captured this call replays correctly with new counts.
+ * max_total bounds offsets[k] + counts[k] (a violating entry is skipped and
+ * reported by nsdf_sync_status as NSDF_ERR_INVALID_ARG) and sizes the launch.
+ * out_n_sdf nullable; points outside every range are left untouched.
+ * Arithmetic: FP32 (the FP32 fused kernel; any precision of the context).
+ * The first call with a given max_total may allocate scratch: make it before
+ * capturing the call into a graph.
  */
 nsdf_status nsdf_query_grouped(nsdf_ctx *ctx, const float *pts,
                                const int64_t *offsets, const int64_t *counts,
                                int64_t max_total, float eps, float *out_pts,
                                float *out_n_sdf, nsdf_stream stream);
+
+/*
+ * Autotuner of the grouped launch: times every tile shape (4 or 8 points per
+ * thread) and every CTAs-per-SM count that fits on this exact problem
+ * (3 timed launches each, CUDA events), keeps the fastest in the context for
+ * later nsdf_query_grouped calls and writes it to chosen[0] (points per
+ * thread) and chosen[1] (CTAs per SM) when chosen is not NULL.  Runs the
+ * problem several times (outputs are overwritten with correct results) and
+ * synchronises `stream`; do not call it during stream capture.
+ */
+nsdf_status nsdf_autotune_grouped(nsdf_ctx *ctx, const float *pts,
+                                  const int64_t *offsets, const int64_t *counts,
+                                  int64_t max_total, float eps, float *out_pts,
+                                  float *out_n_sdf, nsdf_stream stream,
+                                  int *chosen);
+
+/* Set the grouped launch configuration directly (e.g. from a saved tuning):
+ * points_per_thread 4 or 8, ctas_per_sm >= 0 (0: as many as fit). */
+nsdf_status nsdf_set_grouped_config(nsdf_ctx *ctx, int points_per_thread,
+                                    int ctas_per_sm);
 
 /*
  * Ground-truth signed distance to a watertight triangle mesh by brute force

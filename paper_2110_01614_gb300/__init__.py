@@ -23,6 +23,8 @@ __all__ = [
     "NsdfError", "NSDF_FP32", "NSDF_BF16", "NSDF_FP16", "NSDF_RAW_GRADIENT", "make_arch",
     "nsdf_num_params", "nsdf_create", "nsdf_destroy", "nsdf_load_weights",
     "nsdf_query", "nsdf_collide", "nsdf_collide_noalloc", "nsdf_backward", "nsdf_query_grouped",
+    "nsdf_autotune_grouped", "nsdf_set_grouped_config",
+    "nsdf_autotune_grouped", "nsdf_set_grouped_config",
     "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status", "nsdf_debug_inject",
     "nsdf_status_string", "NeuralSDF", "library",
 ]
@@ -141,6 +143,22 @@ def nsdf_query_grouped(ctx, pts, offsets, counts, max_total, eps, out_pts, out_n
     _check(library().nsdf_query_grouped(ctx, _ptr(pts), _ptr(offsets), _ptr(counts),
                                         int(max_total), float(eps), _ptr(out_pts),
                                         _ptr(out_n_sdf), _stream(stream)), "nsdf_query_grouped")
+
+
+def nsdf_autotune_grouped(ctx, pts, offsets, counts, max_total, eps, out_pts, out_n_sdf=None,
+                          stream=None):
+    """Time the grouped launch's tile shapes on this problem; returns (points/thread, CTAs/SM)."""
+    chosen = (ctypes.c_int * 2)()
+    _check(library().nsdf_autotune_grouped(ctx, _ptr(pts), _ptr(offsets), _ptr(counts),
+                                           int(max_total), float(eps), _ptr(out_pts),
+                                           _ptr(out_n_sdf), _stream(stream), chosen),
+           "nsdf_autotune_grouped")
+    return int(chosen[0]), int(chosen[1])
+
+
+def nsdf_set_grouped_config(ctx, points_per_thread, ctas_per_sm):
+    _check(library().nsdf_set_grouped_config(ctx, int(points_per_thread), int(ctas_per_sm)),
+           "nsdf_set_grouped_config")
 
 
 def nsdf_mesh_sdf(verts, faces, pts, out_sdf, stream=None):

@@ -159,6 +159,11 @@ struct nsdf_ctx {
   // bounded waits and test-only fault injection (see include/nsdf_debug.h)
   long long wait_budget = 4000000000LL;   // ~2 s of SM clock per mbarrier wait
   int drop_load = -1;
+  // grouped launches: device table of per-network pointers, work list, tuned shape
+  NetPtrs *d_netptrs = nullptr;
+  int32_t *d_tile_start = nullptr;
+  int grouped_pt = 8;          // points per thread of the FP32 tile (4 or 8)
+  int grouped_cps = 0;         // CTAs per SM (0: as many as fit)
 };
 
 namespace {
@@ -411,6 +416,17 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
     }
   }
   if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_err, 4);
+  if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_netptrs, (size_t)n_nets);
+  if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_tile_start, (size_t)n_nets + 1);
+  if (st == NSDF_OK) {
+    std::vector<NetPtrs> h(n_nets);
+    for (int k = 0; k < n_nets; ++k) {
+      const NetDevice &d = ctx->nets[k];
+      h[k] = NetPtrs{d.w0, d.bias, d.fwd_t, d.bwd, d.wout, d.bout};
+    }
+    st = map_err(cudaMemcpy(ctx->d_netptrs, h.data(), sizeof(NetPtrs) * n_nets,
+                            cudaMemcpyHostToDevice));
+  }
   if (st == NSDF_OK) st = map_err(cudaMemset(ctx->d_err, 0, sizeof(int)));
   if (st != NSDF_OK) {
     nsdf_destroy(ctx);
@@ -605,6 +621,136 @@ nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n, const floa
                                  n_params, s));
 }
 
+namespace {
+
+struct GroupedArgs {
+  const float *pts;
+  const int64_t *offsets, *counts;
+  int64_t max_total;
+  float eps;
+  float *out_pts, *out_n_sdf;
+};
+
+nsdf_status grouped_check(nsdf_ctx *ctx, const GroupedArgs &g) {
+  if (!ctx || g.max_total < 0 || !std::isfinite(g.eps)) return NSDF_ERR_INVALID_ARG;
+  if (g.max_total == 0) return NSDF_OK;
+  if (!g.pts || !g.offsets || !g.counts || !g.out_pts) return NSDF_ERR_INVALID_ARG;
+  if (!aligned16(g.pts) || !aligned16(g.out_pts) || (g.out_n_sdf && !aligned16(g.out_n_sdf)))
+    return NSDF_ERR_MISALIGNED;
+  if ((reinterpret_cast<uintptr_t>(g.offsets) & 7u) || (reinterpret_cast<uintptr_t>(g.counts) & 7u))
+    return NSDF_ERR_MISALIGNED;
+  for (int k = 0; k < ctx->n_nets; ++k)
+    if (!ctx->nets[k].loaded) return NSDF_ERR_NOT_LOADED;
+  if (!query_fp32_supported(ctx->arch.width)) return NSDF_ERR_UNSUPPORTED;
+  return NSDF_OK;
+}
+
+// Grid of a grouped launch for a tile shape and CTAs per SM (0 = as many as fit):
+// enough CTAs for the largest possible work list, at most what is resident.
+int grouped_grid(const nsdf_ctx *ctx, int pt, int cps, int64_t max_total) {
+  const int P = fp32_tile_points(ctx->arch.width, pt);
+  const int fit = fp32_ctas_per_sm(ctx->arch.width, pt);
+  if (cps <= 0 || cps > fit) cps = fit;
+  const int64_t max_tiles = (max_total + P - 1) / P + ctx->n_nets;
+  const int64_t cap = (int64_t)ctx->num_sms * cps;
+  return (int)(max_tiles < cap ? max_tiles : cap);
+}
+
+nsdf_status grouped_launch(nsdf_ctx *ctx, const GroupedArgs &g, int pt, int cps, cudaStream_t s) {
+  const nsdf_arch &a = ctx->arch;
+  const int grid = grouped_grid(ctx, pt, cps, g.max_total);
+  nsdf_status st = ensure_scratch(ctx, fp32_scratch_bytes_pt(a.width, pt, a.n_hidden, grid));
+  if (st != NSDF_OK) return st;
+  cudaError_t e = launch_build_tile_list(g.offsets, g.counts, ctx->n_nets,
+                                         fp32_tile_points(a.width, pt), g.max_total,
+                                         ctx->d_tile_start, ctx->d_err, s);
+  if (e != cudaSuccess) return map_err(e);
+  QueryParams p{};
+  fill_net(ctx, 0, p);
+  p.pts = reinterpret_cast<const float4 *>(g.pts);
+  p.n = g.max_total;
+  p.collide = 1;
+  p.eps = g.eps;
+  p.out_pts = reinterpret_cast<float4 *>(g.out_pts);
+  p.out_n_sdf = reinterpret_cast<float4 *>(g.out_n_sdf);
+  p.scratch = ctx->scratch;
+  p.g_nets = ctx->n_nets;
+  p.g_offsets = g.offsets;
+  p.g_counts = g.counts;
+  p.g_tile_start = ctx->d_tile_start;
+  p.g_netptrs = ctx->d_netptrs;
+  return map_err(launch_query_fp32_grouped(p, pt, grid, s));
+}
+
+}  // namespace
+
+nsdf_status nsdf_query_grouped(nsdf_ctx *ctx, const float *pts, const int64_t *offsets,
+                               const int64_t *counts, int64_t max_total, float eps, float *out_pts,
+                               float *out_n_sdf, nsdf_stream stream) {
+  const GroupedArgs g{pts, offsets, counts, max_total, eps, out_pts, out_n_sdf};
+  nsdf_status st = grouped_check(ctx, g);
+  if (st != NSDF_OK || max_total == 0) return st;
+  return grouped_launch(ctx, g, ctx->grouped_pt, ctx->grouped_cps,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+nsdf_status nsdf_autotune_grouped(nsdf_ctx *ctx, const float *pts, const int64_t *offsets,
+                                  const int64_t *counts, int64_t max_total, float eps,
+                                  float *out_pts, float *out_n_sdf, nsdf_stream stream,
+                                  int *chosen) {
+  const GroupedArgs g{pts, offsets, counts, max_total, eps, out_pts, out_n_sdf};
+  nsdf_status st = grouped_check(ctx, g);
+  if (st != NSDF_OK) return st;
+  if (max_total == 0) return NSDF_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return NSDF_ERR_CUDA;
+  float best = 3.0e38f;
+  int best_pt = ctx->grouped_pt, best_cps = ctx->grouped_cps;
+  const int pts_opts[2] = {4, 8};
+  for (int pt : pts_opts) {
+    const int fit = fp32_ctas_per_sm(ctx->arch.width, pt);
+    for (int cps = 1; cps <= fit; ++cps) {
+      st = grouped_launch(ctx, g, pt, cps, s);             // warm-up (and scratch growth)
+      if (st != NSDF_OK) break;
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 3; ++rep) grouped_launch(ctx, g, pt, cps, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = NSDF_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_pt = pt;
+        best_cps = cps;
+      }
+    }
+    if (st != NSDF_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NSDF_OK) return st;
+  ctx->grouped_pt = best_pt;
+  ctx->grouped_cps = best_cps;
+  if (chosen) {
+    chosen[0] = best_pt;
+    chosen[1] = best_cps;
+  }
+  return NSDF_OK;
+}
+
+nsdf_status nsdf_set_grouped_config(nsdf_ctx *ctx, int points_per_thread, int ctas_per_sm) {
+  if (!ctx || (points_per_thread != 4 && points_per_thread != 8) || ctas_per_sm < 0)
+    return NSDF_ERR_INVALID_ARG;
+  ctx->grouped_pt = points_per_thread;
+  ctx->grouped_cps = ctas_per_sm;
+  return NSDF_OK;
+}
+
 nsdf_status nsdf_sync_status(nsdf_ctx *ctx, nsdf_stream stream) {
   if (!ctx) return NSDF_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -615,7 +761,7 @@ nsdf_status nsdf_sync_status(nsdf_ctx *ctx, nsdf_stream stream) {
   if (e != cudaSuccess) return map_err(e);
   if (h != kDevOk) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
-    return NSDF_ERR_TIMEOUT;
+    return h == kDevBadWork ? NSDF_ERR_INVALID_ARG : NSDF_ERR_TIMEOUT;
   }
   return NSDF_OK;
 }

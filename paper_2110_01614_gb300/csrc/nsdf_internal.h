@@ -17,6 +17,7 @@ namespace nsdf {
 enum DeviceError : int {
   kDevOk = 0,
   kDevTimeout = 1,   // a bounded mbarrier wait gave up
+  kDevBadWork = 2,   // a grouped work list entry lies outside [0, max_total)
 };
 
 // Device copies of one network, in the layouts the kernels read.
@@ -37,6 +38,11 @@ struct NetDevice {
   CUtensorMap tmap_fwd;
   CUtensorMap tmap_bwd;
   bool loaded = false;
+};
+
+// FP32 weight pointers of one network, as a device array for grouped launches.
+struct NetPtrs {
+  const float *w0, *bias, *fwd_t, *bwd, *wout, *bout;
 };
 
 // Everything one fused query launch needs (passed by value).
@@ -68,6 +74,12 @@ struct QueryParams {
   // first-order backward through the query kernel: out_grad[i] = grad_scale[i] * grad f
   const float *grad_scale;   // nullable
   float4 *out_grad;
+  // grouped launch (g_nets > 0): tile t of network k covers points
+  // g_offsets[k] + (t - g_tile_start[k]) * P ... (capped by g_counts[k])
+  int g_nets;
+  const int64_t *g_offsets, *g_counts;
+  const int32_t *g_tile_start;   // [g_nets + 1], built on the device
+  const NetPtrs *g_netptrs;      // [g_nets]
 };
 
 // Launchers (return a cudaError_t from the launch).
@@ -75,6 +87,11 @@ cudaError_t launch_query_fp32(const QueryParams &p, int num_sms, cudaStream_t s)
 size_t query_fp32_scratch_bytes(int width, int n_hidden, int grid);
 int query_fp32_grid(int width, int64_t n, int num_sms);
 bool query_fp32_supported(int width);
+// grouped FP32 launches with a chosen tile shape (pt = points per thread, 4 or 8)
+int fp32_tile_points(int width, int pt);
+int fp32_ctas_per_sm(int width, int pt);
+size_t fp32_scratch_bytes_pt(int width, int pt, int n_hidden, int grid);
+cudaError_t launch_query_fp32_grouped(const QueryParams &p, int pt, int grid, cudaStream_t s);
 
 bool query_tc16_supported(int width, int n_hidden, int skip);
 bool make_tc16_tmaps(NetDevice &net, int width, int n_hidden, bool fp16);
@@ -89,6 +106,10 @@ int query_tc16_min_grid();   // CTAs of one cluster: the smallest grid of the ke
 nsdf_status ctx_query_setup(nsdf_ctx *ctx, QueryParams *p, int *num_sms, int *width,
                             int *n_hidden, bool *tc16, bool *fp16, const NetDevice **net);
 nsdf_status ctx_set_transform(const float *T, QueryParams *p);
+
+cudaError_t launch_build_tile_list(const int64_t *offsets, const int64_t *counts, int n_nets, int P,
+                                   int64_t max_total, int32_t *tile_start, int *err,
+                                   cudaStream_t s);
 
 size_t backward_smem_bytes(int width, int n_hidden, int64_t n_params);
 bool backward_supported(int width, int n_hidden, int64_t n_params);

@@ -25,10 +25,10 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr float kInvSqrt2 = 0.70710678118654752f;
 
-template <int W>
+template <int W, int PT_ = 8>
 struct Cfg {
   static constexpr int WG = (W >= 256) ? 2 : 1;   // warps sharing a point group
-  static constexpr int PT = 8;                     // points per thread
+  static constexpr int PT = PT_;                   // points per thread (tile shape)
   static constexpr int GROUPS = kWarps / WG;
   static constexpr int P = GROUPS * PT;            // points per tile
   static constexpr int CT = W / (32 * WG);         // columns per thread
@@ -66,9 +66,9 @@ __device__ __forceinline__ void softplus_and_slope(float z, float beta, float &h
 }
 
 // Stage rows [k0, k0+KC) of a row-major [W x W] panel into shared memory.
-template <int W>
+template <int W, int PT_ = 8>
 __device__ __forceinline__ void stage_panel(float *dst, const float *src, int k0) {
-  using C = Cfg<W>;
+  using C = Cfg<W, PT_>;
   constexpr int VEC = C::KC * W / 4;
   const float4 *s4 = reinterpret_cast<const float4 *>(src + (size_t)k0 * W);
   float4 *d4 = reinterpret_cast<float4 *>(dst);
@@ -79,19 +79,19 @@ __device__ __forceinline__ void stage_panel(float *dst, const float *src, int k0
 // acc[i][j] = sum_k X[g*PT + i][k] * M[k][col_j] for the thread's PT points
 // and CT columns; M is a global [W x W] row-major panel streamed through
 // two shared buffers.  All threads of the CTA must call this together.
-template <int W>
+template <int W, int PT_ = 8>
 __device__ __forceinline__ void panel_product(const float *X, const float *M, float *Ms,
                                               int g, int colbase,
-                                              float (&acc)[Cfg<W>::PT][Cfg<W>::CT]) {
-  using C = Cfg<W>;
+                                              float (&acc)[Cfg<W, PT_>::PT][Cfg<W, PT_>::CT]) {
+  using C = Cfg<W, PT_>;
 #pragma unroll
   for (int i = 0; i < C::PT; ++i)
 #pragma unroll
     for (int j = 0; j < C::CT; ++j) acc[i][j] = 0.0f;
-  stage_panel<W>(Ms, M, 0);
+  stage_panel<W, PT_>(Ms, M, 0);
   for (int kc = 0; kc < C::NCHUNK; ++kc) {
     if (kc + 1 < C::NCHUNK) {
-      stage_panel<W>(Ms + ((kc + 1) & 1) * C::KC * W, M, (kc + 1) * C::KC);
+      stage_panel<W, PT_>(Ms + ((kc + 1) & 1) * C::KC * W, M, (kc + 1) * C::KC);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -121,9 +121,9 @@ __device__ __forceinline__ void panel_product(const float *X, const float *M, fl
   }
 }
 
-template <int W>
+template <int W, int PT_ = 8>
 __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm) {
-  using C = Cfg<W>;
+  using C = Cfg<W, PT_>;
   extern __shared__ float4 smem4[];
   float *smem = reinterpret_cast<float *>(smem4);
   float *X = smem + C::X_OFF;
@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
   const int skip = prm.skip;
   const int nshort = W - 3;   // outputs of the layer feeding the skip
   const float beta = prm.beta;
-  const int64_t ntiles = (prm.n + C::P - 1) / C::P;
+  const bool grouped = prm.g_nets > 0;
+  const int64_t ntiles = grouped ? (int64_t)prm.g_tile_start[prm.g_nets] : (prm.n + C::P - 1) / C::P;
   // per-CTA slope slab: [L-1][PT][CT][kThreads]
   float *slab = prm.scratch + (size_t)blockIdx.x * (size_t)(L - 1) * C::P * W;
   auto slot = [&](int l, int i, int j) -> float * {
@@ -148,12 +149,31 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
   };
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t base = tile * C::P;
+    // the tile's points [base, base + nvalid) and its network
+    int64_t base, nvalid;
+    const float *w0 = prm.w0, *bias = prm.bias, *fwd_t = prm.fwd_t, *bwdw = prm.bwd,
+                *wout = prm.wout, *bout = prm.bout;
+    if (grouped) {
+      int lo = 0, hi = prm.g_nets;               // last k with tile_start[k] <= tile
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prm.g_tile_start[mid] <= tile) lo = mid; else hi = mid;
+      }
+      const int64_t local = tile - prm.g_tile_start[lo];
+      base = prm.g_offsets[lo] + local * C::P;
+      nvalid = prm.g_counts[lo] - local * C::P;
+      const NetPtrs &np = prm.g_netptrs[lo];
+      w0 = np.w0; bias = np.bias; fwd_t = np.fwd_t; bwdw = np.bwd; wout = np.wout; bout = np.bout;
+    } else {
+      base = tile * C::P;
+      nvalid = prm.n - base;
+    }
+    if (nvalid > C::P) nvalid = C::P;
     // ---- a1: point load (+ T^{-1}) ----
     if (tid < C::P) {
       int64_t idx = base + tid;
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (idx < prm.n) p = prm.pts[idx];
+      if (tid < nvalid) p = prm.pts[idx];
       if (prm.has_T) {
         const float *t = prm.Ti;
         float x = t[0] * p.x + t[1] * p.y + t[2] * p.z + t[3];
@@ -176,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
 #pragma unroll
     for (int j = 0; j < C::CT; ++j) {
       const int c = colbase + 32 * j;
-      const float w0x = prm.w0[c * 3 + 0], w0y = prm.w0[c * 3 + 1], w0z = prm.w0[c * 3 + 2];
+      const float w0x = w0[c * 3 + 0], w0y = w0[c * 3 + 1], w0z = w0[c * 3 + 2];
 #pragma unroll
       for (int i = 0; i < C::PT; ++i) {
         float4 p = Ps[g * C::PT + i];
@@ -188,16 +208,16 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
     for (int l = 0; l < L; ++l) {
       if (l > 0) {
         float *t = X; X = Y; Y = t;
-        panel_product<W>(X, prm.fwd_t + (size_t)(l - 1) * W * W, Ms, g, colbase, acc);
+        panel_product<W, PT_>(X, fwd_t + (size_t)(l - 1) * W * W, Ms, g, colbase, acc);
       }
-      const float *b = prm.bias + (size_t)l * W;
+      const float *b = bias + (size_t)l * W;
       const bool last = (l == L - 1);
       const bool feeds_skip = (skip > 0 && l == skip - 1);
 #pragma unroll
       for (int j = 0; j < C::CT; ++j) {
         const int c = colbase + 32 * j;
         const float bc = b[c];
-        const float wo = last ? prm.wout[c] : 0.0f;
+        const float wo = last ? wout[c] : 0.0f;
 #pragma unroll
         for (int i = 0; i < C::PT; ++i) {
           float h, s;
@@ -240,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
     for (int i = 0; i < C::PT; ++i) gp[i][0] = gp[i][1] = gp[i][2] = 0.0f;
     for (int l = L - 1; l >= 1; --l) {
       float *t = X; X = Y; Y = t;                       // X = delta_l
-      panel_product<W>(X, prm.bwd + (size_t)(l - 1) * W * W, Ms, g, colbase, acc);
+      panel_product<W, PT_>(X, bwdw + (size_t)(l - 1) * W * W, Ms, g, colbase, acc);
       const bool at_skip = (skip > 0 && l == skip);
 #pragma unroll
       for (int j = 0; j < C::CT; ++j) {
@@ -260,9 +280,9 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
           if (l - 1 > 0) {
             Y[pr * W + c] = d;
           } else {
-            gp[i][0] = fmaf(d, prm.w0[c * 3 + 0], gp[i][0]);
-            gp[i][1] = fmaf(d, prm.w0[c * 3 + 1], gp[i][1]);
-            gp[i][2] = fmaf(d, prm.w0[c * 3 + 2], gp[i][2]);
+            gp[i][0] = fmaf(d, w0[c * 3 + 0], gp[i][0]);
+            gp[i][1] = fmaf(d, w0[c * 3 + 1], gp[i][1]);
+            gp[i][2] = fmaf(d, w0[c * 3 + 2], gp[i][2]);
           }
         }
       }
@@ -276,9 +296,9 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
 #pragma unroll
         for (int i = 0; i < C::PT; ++i) {
           const float d = Y[(g * C::PT + i) * W + c];
-          gp[i][0] = fmaf(d, prm.w0[c * 3 + 0], gp[i][0]);
-          gp[i][1] = fmaf(d, prm.w0[c * 3 + 1], gp[i][1]);
-          gp[i][2] = fmaf(d, prm.w0[c * 3 + 2], gp[i][2]);
+          gp[i][0] = fmaf(d, w0[c * 3 + 0], gp[i][0]);
+          gp[i][1] = fmaf(d, w0[c * 3 + 1], gp[i][1]);
+          gp[i][2] = fmaf(d, w0[c * 3 + 2], gp[i][2]);
         }
       }
     }
@@ -298,13 +318,13 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
     if (tid < C::P) {
       const int64_t idx = base + tid;
       float gx = dir[tid * 4 + 0], gy = dir[tid * 4 + 1], gz = dir[tid * 4 + 2];
-      float f = prm.bout[0];
+      float f = bout[0];
 #pragma unroll
       for (int q = 0; q < C::WG; ++q) {
         const float *r = red + (q * C::P + tid) * 4;
         gx += r[0]; gy += r[1]; gz += r[2]; f += r[3];
       }
-      if (idx < prm.n) {
+      if (tid < nvalid) {
         const float nrm = sqrtf(gx * gx + gy * gy + gz * gz);
         float nx = 0.f, ny = 0.f, nz = 0.f;
         if (nrm >= 1e-20f) { nx = gx / nrm; ny = gy / nrm; nz = gz / nrm; }
@@ -338,9 +358,31 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
   }
 }
 
-template <int W>
+template <int W, int PT_>
+int per_sm_w() {
+  using C = Cfg<W, PT_>;
+  int per_sm = 1;
+  cudaFuncSetAttribute(query_fp32_kernel<W, PT_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)C::SMEM_BYTES);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, query_fp32_kernel<W, PT_>, kThreads,
+                                                C::SMEM_BYTES);
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+template <int W, int PT_>
+cudaError_t launch_grouped_w(const QueryParams &p, int grid, cudaStream_t s) {
+  using C = Cfg<W, PT_>;
+  cudaError_t e = cudaFuncSetAttribute(query_fp32_kernel<W, PT_>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  query_fp32_kernel<W, PT_><<<grid, kThreads, C::SMEM_BYTES, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int W, int PT_ = 8>
 cudaError_t launch_w(const QueryParams &p, int num_sms, cudaStream_t s) {
-  using C = Cfg<W>;
+  using C = Cfg<W, PT_>;
   auto k = query_fp32_kernel<W>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::SMEM_BYTES);
@@ -350,9 +392,9 @@ cudaError_t launch_w(const QueryParams &p, int num_sms, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int W>
+template <int W, int PT_ = 8>
 int grid_w(int64_t n, int num_sms) {
-  using C = Cfg<W>;
+  using C = Cfg<W, PT_>;
   int per_sm = 1;
   // The occupancy of a kernel above 48 KB of dynamic shared memory is only
   // known once its opt-in attribute is set; set it before asking, so that the
@@ -395,6 +437,38 @@ size_t query_fp32_scratch_bytes(int width, int n_hidden, int grid) {
   }
   const int slabs = n_hidden > 1 ? n_hidden - 1 : 1;
   return sizeof(float) * (size_t)grid * slabs * P * width;
+}
+
+#define NSDF_FP32_WIDTHS(X) X(32) X(64) X(128) X(256) X(512)
+
+int fp32_tile_points(int width, int pt) {
+#define CASE(W) \
+  if (width == W) return pt == 4 ? Cfg<W, 4>::P : Cfg<W, 8>::P;
+  NSDF_FP32_WIDTHS(CASE)
+#undef CASE
+  return 0;
+}
+
+int fp32_ctas_per_sm(int width, int pt) {
+#define CASE(W) \
+  if (width == W) return pt == 4 ? per_sm_w<W, 4>() : per_sm_w<W, 8>();
+  NSDF_FP32_WIDTHS(CASE)
+#undef CASE
+  return 1;
+}
+
+size_t fp32_scratch_bytes_pt(int width, int pt, int n_hidden, int grid) {
+  const int slabs = n_hidden > 1 ? n_hidden - 1 : 1;
+  return sizeof(float) * (size_t)grid * slabs * fp32_tile_points(width, pt) * width;
+}
+
+cudaError_t launch_query_fp32_grouped(const QueryParams &p, int pt, int grid, cudaStream_t s) {
+#define CASE(W)                                                                 \
+  if (p.width == W)                                                             \
+    return pt == 4 ? launch_grouped_w<W, 4>(p, grid, s) : launch_grouped_w<W, 8>(p, grid, s);
+  NSDF_FP32_WIDTHS(CASE)
+#undef CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_query_fp32(const QueryParams &p, int num_sms, cudaStream_t s) {
