@@ -55,7 +55,7 @@ class MeshFit:
         self.opt.step()
         self.sched.step()
         self.step_index += 1
-        return float(loss), float(l1), float(eik)
+        return float(loss.detach()), float(l1.detach()), float(eik.detach())
 
     def run(self, steps, log_every=0):
         hist = []

@@ -19,11 +19,12 @@ from .points import (uniform_cube, ellipsoid_shell, body_scale_points,
 from .mesh import icosphere, displaced_icosphere, box_mesh, value_noise
 from .cloth import cloth_grid, spring_list
 from .counts import grouped_counts
+from .training import training_points
 
 __all__ = [
     "Stream", "splitmix64", "Arch", "geometric_init", "layer_shapes",
     "n_params", "unpack", "uniform_cube", "ellipsoid_shell",
     "body_scale_points", "uniform_cube_points", "icosphere",
     "displaced_icosphere", "box_mesh", "value_noise", "cloth_grid",
-    "spring_list", "grouped_counts",
+    "spring_list", "grouped_counts", "training_points",
 ]
