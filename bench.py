@@ -41,6 +41,26 @@ METRIC = "SDF+normal queries/s @1M pts (BF16 tensor cores, FP32 accumulate)"
 MAC_PER_QUERY = 3_670_528
 FLOP_PER_QUERY = 2 * MAC_PER_QUERY
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the tensor-core kernel on this workload, from one ncu capture, keyed by the
+# SHA-256 of the kernel source it was taken on; reported only while the
+# source is unchanged.
+TRAFFIC_CAPTURE = {
+    "source_sha256": "e32f0553d07b5b8898b11be6faa6f41363eec2a2f2049a1e5cd469707acbc18e",
+    "bytes_per_launch": 2.910098e9 + 3.495056e9,
+}
+
+
+def traffic_bytes():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2110_01614_gb300", "csrc", "query_tc16.cu")
+    try:
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return TRAFFIC_CAPTURE["bytes_per_launch"] if h == TRAFFIC_CAPTURE["source_sha256"] else None
+
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -307,8 +327,11 @@ def run_gpu(args):
         "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
                      "peak_source": f"{peak_kind} bf16_tflops (burst, cuBLAS)",
-                     "traffic": None, "kernel": "query_bf16_kernel",
-                     "algorithmic_flop_per_launch": FLOP_PER_QUERY * n},
+                     "traffic": traffic_bytes() if n == N_POINTS else None,
+                     "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                     "kernel": "query_tc16_kernel<bf16>",
+                     "algorithmic_flop_per_launch": FLOP_PER_QUERY * n,
+                     "algorithmic_io_bytes_per_launch": 49 * n},
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": n * 16,
                 "d2h_bytes_per_step": n * (16 + 16 + 1)},
         "forms": {name: {"value": o["value"], "unit": "queries/s", "ms_per_step": o["ms_per_step"],
