@@ -1,0 +1,123 @@
+"""Timings of the support workloads around the collision query (one JSON line each).
+
+* fit: one fitting step of the 3-64-64-64-1 network to the displaced
+  icosphere (20,480 triangles) with 250,000 points: brute-force mesh SDF
+  targets + forward + hand-written backward + Adam (Sec. 3.1).
+* penalty: gradient of sum max(0, eps - f)^2 with respect to 1,048,576 vertices.
+* grouped: 16 networks of the 3-64-64-64-1 shape with log-uniform counts in
+  [2k, 400k] (about 1.2M points) in one grouped launch, autotuned, replayed
+  from a CUDA graph.
+* cloth: 1024 x 1024 cloth, per-step time of Verlet + collision solve for the
+  body-scale network in BF16 / FP16 / FP32, and of the exact brute-force mesh
+  SDF of every vertex (20,480 triangles) as the plain reference.
+
+Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped cloth]
+"""
+
+import json
+import statistics
+import sys
+import time
+
+import numpy as np
+import torch
+
+import synth
+
+from . import (NSDF_BF16, NSDF_FP16, NSDF_FP32, NeuralSDF, nsdf_query_grouped,
+               nsdf_sync_status)
+from .cloth_sim import ClothSim, mesh_reference_step_ms
+from .fit import MeshFit, penalty_gradient
+from .tune import tuned_grouped
+
+TINY = synth.Arch(3, 64, 3, -1, 100.0)
+BODY = synth.Arch(3, 512, 8, 4, 100.0)
+
+
+def events_ms(fn, reps):
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def bench_fit(steps=20):
+    V, F = synth.displaced_icosphere(level=5, seed=7)
+    fit = MeshFit(TINY, V, F, n_points=250_000)
+    fit.run(3)
+    hist, per_step = fit.run(steps)
+    return {"workload": "fit", "points_per_step": 250_000, "triangles": int(F.shape[0]),
+            "s_per_step": per_step, "loss_first": hist[0][0], "loss_last": hist[-1][0]}
+
+
+def bench_penalty(reps=10):
+    net = NeuralSDF(TINY, NSDF_FP32)
+    blob = torch.from_numpy(synth.geometric_init(TINY, 0)).cuda()
+    pts = torch.from_numpy(synth.body_scale_points(1 << 20, 4)).cuda()
+    ms = events_ms(lambda: penalty_gradient(net, blob, pts, 0.002), reps)
+    net.close()
+    return {"workload": "penalty_gradient", "vertices": 1 << 20, "ms": ms}
+
+
+def bench_grouped(reps=20):
+    counts = synth.grouped_counts()
+    offs = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    total = int(counts.sum())
+    net = NeuralSDF(TINY, NSDF_FP32, n_nets=16)
+    for k in range(16):
+        net.load(synth.geometric_init(TINY, k), net=k)
+    P = torch.from_numpy(synth.body_scale_points(total, 5)).cuda()
+    O = torch.from_numpy(offs).cuda()
+    C = torch.from_numpy(counts.astype(np.int64)).cuda()
+    out, ns = torch.empty_like(P), torch.empty_like(P)
+    pt, cps = tuned_grouped(net, P, O, C, total, 0.002, out, ns)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        nsdf_query_grouped(net.ctx, P, O, C, total, 0.002, out, ns)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        nsdf_query_grouped(net.ctx, P, O, C, total, 0.002, out, ns)
+    ms = events_ms(g.replay, reps)
+    nsdf_sync_status(net.ctx)
+    net.close()
+    return {"workload": "grouped", "nets": 16, "points": total, "ms": ms,
+            "queries_per_s": total / (ms * 1e-3), "tile_points_per_thread": pt, "ctas_per_sm": cps,
+            "precision": "fp32"}
+
+
+def bench_cloth(steps=20):
+    res = {"workload": "cloth", "grid": "1024x1024", "steps": steps}
+    blob = synth.geometric_init(BODY, 0)
+    for name, prec in (("bf16", NSDF_BF16), ("fp16", NSDF_FP16), ("fp32", NSDF_FP32)):
+        body = NeuralSDF(BODY, prec).load(blob)
+        sim = ClothSim(n=1024)
+        sim.run(body, 2)
+        ts = sim.run(body, steps if name != "fp32" else 3)
+        res[f"{name}_ms_per_step"] = statistics.median(ts)
+        body.close()
+    V, F = synth.displaced_icosphere(level=5, seed=7)
+    sim = ClothSim(n=1024)
+    ms, _ = mesh_reference_step_ms(V, F, sim.x, repeats=2)
+    res["mesh_bruteforce_sdf_ms_per_step"] = ms
+    return res
+
+
+def main(argv):
+    which = argv or ["fit", "penalty", "grouped", "cloth"]
+    torch.cuda.set_device(0)
+    for w in which:
+        t0 = time.perf_counter()
+        r = {"fit": bench_fit, "penalty": bench_penalty, "grouped": bench_grouped,
+             "cloth": bench_cloth}[w]()
+        r["wall_s"] = time.perf_counter() - t0
+        print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
