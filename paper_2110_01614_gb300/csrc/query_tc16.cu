@@ -295,6 +295,39 @@ __device__ __forceinline__ void l2_prefetch_bulk(const void *src, uint32_t bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// Two elements at once in packed FP16 (used where the result is rounded to 16
+// bits anyway): u = 2^(-beta log2(e) |z|) on the MUFU in f16x2, log1p(u) =
+// u P(u) with the same polynomial in HFMA2, and the slope as
+// sigmoid(beta z) = (1 + tanh(beta z / 2)) / 2 with tanh in f16x2.  The
+// pre-activation is rounded to FP16 first (relative 2^-11).
+__device__ __forceinline__ __half2 h2_ex2(__half2 x) {
+  uint32_t y, xi = *reinterpret_cast<uint32_t *>(&x);
+  asm("ex2.approx.f16x2 %0, %1;\n" : "=r"(y) : "r"(xi));
+  return *reinterpret_cast<__half2 *>(&y);
+}
+__device__ __forceinline__ __half2 h2_tanh(__half2 x) {
+  uint32_t y, xi = *reinterpret_cast<uint32_t *>(&x);
+  asm("tanh.approx.f16x2 %0, %1;\n" : "=r"(y) : "r"(xi));
+  return *reinterpret_cast<__half2 *>(&y);
+}
+struct ActH2 {          // per-kernel constants of act_h2
+  __half2 neg_bl2e, inv_beta, half_beta;
+};
+__device__ __forceinline__ void act_h2(float z0, float z1, const ActH2 &k, __half2 &h, __half2 &s) {
+  const __half2 zh = __floats2half2_rn(z0, z1);
+  const __half2 u = h2_ex2(__hmul2(__habs2(zh), k.neg_bl2e));
+  __half2 p = __float2half2_rn(-2.344365580e-02f);
+  p = __hfma2(p, u, __float2half2_rn(1.001397327e-01f));
+  p = __hfma2(p, u, __float2half2_rn(-2.090795360e-01f));
+  p = __hfma2(p, u, __float2half2_rn(3.248495807e-01f));
+  p = __hfma2(p, u, __float2half2_rn(-4.993146523e-01f));
+  p = __hfma2(p, u, __float2half2_rn(9.999905920e-01f));
+  h = __hfma2(__hmul2(u, p), k.inv_beta, __hmax2(zh, __float2half2_rn(0.0f)));
+  const __half2 half = __float2half2_rn(0.5f);
+  s = __hfma2(h2_tanh(__hmul2(zh, k.half_beta)), half, half);
+}
+__device__ __forceinline__ uint32_t h2_bits(__half2 v) { return *reinterpret_cast<uint32_t *>(&v); }
+
 __device__ __forceinline__ float4 ldg4(const float *p) {
   return __ldg(reinterpret_cast<const float4 *>(p));
 }
@@ -324,6 +357,7 @@ struct Epi {
   const float *wsk;     // three rows of W: W_s[:, nshort + j]
   uint64_t pol;         // L2 evict-last policy for slope stores
   int lane;
+  ActH2 kh;             // packed-FP16 activation constants
   // slope chunk j (8 values, 16 B) of layer l for this row / half
   __device__ __forceinline__ uint4 *slope(int l, int j) const {
     return reinterpret_cast<uint4 *>(slab + ((((size_t)l * 2 + ch) * 32 + j) * kM + r) * 16);
@@ -338,6 +372,45 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
                                           Acc &acc) {
   const float *b = e.bias + (size_t)l * kW + c0;
   uint32_t hw[16], sw[16];
+  if constexpr (!LAST && !FEEDS_SKIP) {
+    // activations and slopes in packed FP16; slopes are kept as FP16 in the slab
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 bq = ldg4(b + 4 * q);
+      float4 s0, s1, s2;
+      if (AT_SKIP) {
+        s0 = ldg4(e.wsk + c0 + 4 * q);
+        s1 = ldg4(e.wsk + kW + c0 + 4 * q);
+        s2 = ldg4(e.wsk + 2 * kW + c0 + 4 * q);
+      }
+      float z[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        z[u] = __uint_as_float(raw[4 * q + u]) + comp(bq, u);
+        if (AT_SKIP)
+          z[u] = fmaf(kInvSqrt2, fmaf(comp(s0, u), e.px, fmaf(comp(s1, u), e.py, comp(s2, u) * e.pz)), z[u]);
+      }
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        __half2 h, sl;
+        act_h2(z[2 * v], z[2 * v + 1], e.kh, h, sl);
+        if (kF16) {
+          hw[2 * q + v] = h2_bits(h);
+        } else {
+          const float2 hf = __half22float2(h);
+          hw[2 * q + v] = Op<false>::pack(hf.x, hf.y);
+        }
+        sw[2 * q + v] = h2_bits(sl);
+      }
+    }
+    store_a_chunk(e.A, e.r, c0, hw);
+    const int j0 = (c0 - 256 * e.ch) >> 3;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      st_slope(e.slope(l, j0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
+               e.pol);
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const float4 bq = ldg4(b + 4 * q);
@@ -372,8 +445,8 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
     }
     hw[2 * q] = Op<kF16>::pack(hv[0], hv[1]);
     hw[2 * q + 1] = Op<kF16>::pack(hv[2], hv[3]);
-    sw[2 * q] = Op<kF16>::pack(sv[0], sv[1]);
-    sw[2 * q + 1] = Op<kF16>::pack(sv[2], sv[3]);
+    sw[2 * q] = Op<true>::pack(sv[0], sv[1]);
+    sw[2 * q + 1] = Op<true>::pack(sv[2], sv[3]);
   }
   store_a_chunk(e.A, e.r, c0, hw);
   if (!LAST) {
@@ -427,8 +500,8 @@ __device__ __forceinline__ void layer0(const Epi &e) {
       }
       hw[2 * q] = Op<kF16>::pack(hv[0], hv[1]);
       hw[2 * q + 1] = Op<kF16>::pack(hv[2], hv[3]);
-      sw[2 * q] = Op<kF16>::pack(sv[0], sv[1]);
-      sw[2 * q + 1] = Op<kF16>::pack(sv[2], sv[3]);
+      sw[2 * q] = Op<true>::pack(sv[0], sv[1]);
+      sw[2 * q + 1] = Op<true>::pack(sv[2], sv[3]);
     }
     store_a_chunk(e.A, e.r, c0, hw);
 #pragma unroll
@@ -457,8 +530,8 @@ __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (
       w_c = ldg4(e.w0 + 3 * (c0 + 4 * q) + 8);
     }
     const uint32_t swords[2] = {comp_u(sl[q >> 1], 2 * (q & 1)), comp_u(sl[q >> 1], 2 * (q & 1) + 1)};
-    const float2 sa = Op<kF16>::unpack(swords[0]);
-    const float2 sb = Op<kF16>::unpack(swords[1]);
+    const float2 sa = Op<true>::unpack(swords[0]);     // slopes are FP16 in the slab
+    const float2 sb = Op<true>::unpack(swords[1]);
     const float sv[4] = {sa.x, sa.y, sb.x, sb.y};
     float dv[4];
 #pragma unroll
@@ -699,6 +772,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the transposed copy (row k = nshort + j holds W_s[n][k] over n)
     e.wsk = skip > 0 ? prm.fwd_t + ((size_t)(skip - 1) * kW + kNShort) * kW : prm.fwd_t;
     e.pol = l2_evict_last_policy();
+    e.kh.neg_bl2e = __float2half2_rn(-prm.beta * 1.4426950408889634f);
+    e.kh.inv_beta = __float2half2_rn(1.0f / prm.beta);
+    e.kh.half_beta = __float2half2_rn(0.5f * prm.beta);
     e.lane = lane;
     const bool prefetcher = (warp == 2 && lane == 0);
     uint32_t d_phase = 0, x_phase = 0;
