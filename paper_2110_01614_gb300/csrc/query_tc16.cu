@@ -26,10 +26,20 @@
 //
 // Warp roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
 // TMEM owner, warps 2..9 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31;
-// warps 2..5 take columns 0..255 of every layer, warps 6..9 columns
-// 256..511).  Producer, MMA and epilogue hand over through mbarriers; every
-// wait is bounded (QueryParams::wait_budget cycles) and on expiry the kernel
-// records kDevTimeout, drains what it has in flight and returns.
+// of each 256-column half of a layer, warps 2..5 take the first 128
+// columns, warps 6..9 the last 128).  Producer, MMA and epilogue hand over
+// through mbarriers; every wait is bounded (QueryParams::wait_budget cycles)
+// and on expiry the kernel records kDevTimeout, drains what it has in flight
+// and returns.
+//
+// Products and epilogues overlap within a tile.  Each product runs as four
+// quarter products in the order (half 0, K 0..255), (half 0, K 256..511),
+// (half 1, K 0..255), (half 1, K 256..511), half h landing in TMEM columns
+// 256h..256h+255.  The epilogue of half 0 starts as soon as its products are
+// done and runs while half 1 is multiplied; it rewrites A's columns 0..255
+// only once the (half 1, K 0..255) products have read them.  The next
+// layer's (half 0, K 0..255) products then start while the epilogue of half 1
+// still runs.
 
 #include <cudaTypedefs.h>
 
@@ -61,8 +71,9 @@ constexpr float kInvSqrt2 = 0.70710678118654752f;
 constexpr int kOffA = 0;
 constexpr int kOffB = kOffA + kABytes;
 constexpr int kOffBar = kOffB + kStages * kStageBytes;
-// barriers: full[kStages], empty[kStages], a_ready, d_full, mma_done, x_full, x_empty
-constexpr int kNumBars = 2 * kStages + 5;
+// barriers: full[kStages], empty[kStages], a_lo, a_hi, d0_full, d1_full,
+// lo_free, mma_done, x_full, x_empty
+constexpr int kNumBars = 2 * kStages + 8;
 constexpr int kOffTmemSlot = kOffBar + 8 * kNumBars;
 constexpr int kOffAbort = kOffTmemSlot + 4;
 constexpr int kOffExch = ((kOffAbort + 4 + 15) / 16) * 16;   // float4 [kM]
@@ -343,12 +354,28 @@ struct Acc {
   float gx = 0.f, gy = 0.f, gz = 0.f, f = 0.f;
 };
 
+// The wait an epilogue of column half 0 passes before its first write to A:
+// the (half 1, K 0..255) products must have read A's columns 0..255.
+struct Gate {
+  uint32_t bar, parity;
+  long long budget;
+  volatile int *abort;
+  bool pending, ok;
+  __device__ __forceinline__ void pass() {
+    if (pending) {
+      pending = false;
+      ok = mbar_wait(bar, parity, budget, abort);
+      tc_fence_after();
+    }
+  }
+};
+
 // Per-thread state of an epilogue thread for one tile.
 struct Epi {
   uint8_t *A;
   uint8_t *slab;        // this CTA's slope slab
   uint32_t t_row;       // TMEM address of lane 32*q, column 0
-  int r, ch;            // tile row (= TMEM lane) and column half
+  int r, ch;            // tile row (= TMEM lane); which 128 columns of each half
   float neg_bl2e, inv_beta;
   float px, py, pz;     // query point in the body frame
   const float *bias;    // [n_hidden][W]
@@ -358,9 +385,9 @@ struct Epi {
   uint64_t pol;         // L2 evict-last policy for slope stores
   int lane;
   ActH2 kh;             // packed-FP16 activation constants
-  // slope chunk j (8 values, 16 B) of layer l for this row / half
-  __device__ __forceinline__ uint4 *slope(int l, int j) const {
-    return reinterpret_cast<uint4 *>(slab + ((((size_t)l * 2 + ch) * 32 + j) * kM + r) * 16);
+  // slopes of layer l, columns 8g..8g+7 (16 B) of this row
+  __device__ __forceinline__ uint4 *slope(int l, int g) const {
+    return reinterpret_cast<uint4 *>(slab + (((size_t)l * (kW / 8) + g) * kM + r) * 16);
   }
 };
 
@@ -369,7 +396,7 @@ constexpr int kNShort = kW - 3;
 // One 32-column chunk of a forward epilogue (layers 1 .. L-1).
 template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP>
 __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uint32_t (&raw)[32],
-                                          Acc &acc) {
+                                          Acc &acc, Gate &gate) {
   const float *b = e.bias + (size_t)l * kW + c0;
   uint32_t hw[16], sw[16];
   if constexpr (!LAST && !FEEDS_SKIP) {
@@ -403,12 +430,13 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
         sw[2 * q + v] = h2_bits(sl);
       }
     }
-    store_a_chunk(e.A, e.r, c0, hw);
-    const int j0 = (c0 - 256 * e.ch) >> 3;
+    const int g0 = c0 >> 3;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      st_slope(e.slope(l, j0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
+      st_slope(e.slope(l, g0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
                e.pol);
+    gate.pass();
+    store_a_chunk(e.A, e.r, c0, hw);
     return;
   }
 #pragma unroll
@@ -448,30 +476,32 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
     sw[2 * q] = Op<true>::pack(sv[0], sv[1]);
     sw[2 * q + 1] = Op<true>::pack(sv[2], sv[3]);
   }
-  store_a_chunk(e.A, e.r, c0, hw);
   if (!LAST) {
-    const int j0 = (c0 - 256 * e.ch) >> 3;
+    const int g0 = c0 >> 3;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      st_slope(e.slope(l, j0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
+      st_slope(e.slope(l, g0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
                e.pol);
   }
+  gate.pass();
+  store_a_chunk(e.A, e.r, c0, hw);
 }
 
-// A forward epilogue over the thread's 256 columns, TMEM loads double-buffered.
+// A forward epilogue over the thread's 128 columns of column half h, TMEM
+// loads double-buffered.
 template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP>
-__device__ __forceinline__ void fwd_layer(const Epi &e, int l, Acc &acc) {
+__device__ __forceinline__ void fwd_half(const Epi &e, int l, int h, Acc &acc, Gate &gate) {
   uint32_t ra[32], rb[32];
-  const int cbase = 256 * e.ch;
+  const int cbase = 256 * h + 128 * e.ch;
   tmem_ld32_async(e.t_row + cbase, ra);
 #pragma unroll 1
-  for (int cc = 0; cc < 8; cc += 2) {
+  for (int cc = 0; cc < 4; cc += 2) {
     tmem_wait_ld(ra);
     tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
-    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * cc, ra, acc);
+    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * cc, ra, acc, gate);
     tmem_wait_ld(rb);
-    if (cc + 2 < 8) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
-    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * (cc + 1), rb, acc);
+    if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
+    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * (cc + 1), rb, acc, gate);
   }
 }
 
@@ -506,7 +536,7 @@ __device__ __forceinline__ void layer0(const Epi &e) {
     store_a_chunk(e.A, e.r, c0, hw);
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      st_slope(e.slope(0, 4 * cc + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
+      st_slope(e.slope(0, (c0 >> 3) + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
                e.pol);
   }
 }
@@ -514,7 +544,7 @@ __device__ __forceinline__ void layer0(const Epi &e) {
 // One 32-column chunk of a reverse epilogue: delta_{l-1} = slope_{l-1} * g.
 template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT>
 __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (&raw)[32],
-                                          const uint4 (&sl)[4], Acc &acc) {
+                                          const uint4 (&sl)[4], Acc &acc, Gate &gate) {
   uint32_t dw[16];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -557,47 +587,53 @@ __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (
     dw[2 * q] = Op<kF16>::pack(dv[0], dv[1]);
     dw[2 * q + 1] = Op<kF16>::pack(dv[2], dv[3]);
   }
-  if (!TO_INPUT) store_a_chunk(e.A, e.r, c0, dw);
+  if (!TO_INPUT) {
+    gate.pass();
+    store_a_chunk(e.A, e.r, c0, dw);
+  }
 }
 
 // After a chunk's slopes have been consumed, drop their L2 lines: the warp's
-// 32 rows x 4 slope groups cover 16 lines of 128 bytes, one per lane 0..15.
-__device__ __forceinline__ void discard_chunk(const Epi &e, int l, int cc) {
+// 32 rows x 4 slope groups (columns c0..c0+31) cover 16 lines of 128 bytes,
+// one per lane 0..15.
+__device__ __forceinline__ void discard_chunk(const Epi &e, int l, int c0) {
   __syncwarp();
   if (e.lane < 16) {
-    const int j = 4 * cc + (e.lane >> 2);
+    const int g = (c0 >> 3) + (e.lane >> 2);
     const int row0 = (e.r & ~31) + 8 * (e.lane & 3);
-    const uint8_t *line = e.slab + ((((size_t)l * 2 + e.ch) * 32 + j) * kM + row0) * 16;
+    const uint8_t *line = e.slab + (((size_t)l * (kW / 8) + g) * kM + row0) * 16;
     l2_discard_line(line);
   }
 }
 
-// A reverse epilogue over the thread's 256 columns: TMEM loads and the
-// slopes of the next chunk are fetched while the current chunk is processed.
+// A reverse epilogue over the thread's 128 columns of column half h: TMEM
+// loads and the slopes of the next chunk are fetched while the current chunk
+// is processed.
 template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT>
-__device__ __forceinline__ void bwd_layer(const Epi &e, int l, Acc &acc) {
+__device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, Gate &gate) {
   uint32_t ra[32], rb[32];
   uint4 sa[4], sb[4];
-  const int cbase = 256 * e.ch;
+  const int cbase = 256 * h + 128 * e.ch;
+  const int g0 = cbase >> 3;
 #pragma unroll
-  for (int t = 0; t < 4; ++t) sa[t] = *e.slope(l - 1, t);
+  for (int t = 0; t < 4; ++t) sa[t] = *e.slope(l - 1, g0 + t);
   tmem_ld32_async(e.t_row + cbase, ra);
 #pragma unroll 1
-  for (int cc = 0; cc < 8; cc += 2) {
+  for (int cc = 0; cc < 4; cc += 2) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) sb[t] = *e.slope(l - 1, 4 * (cc + 1) + t);
+    for (int t = 0; t < 4; ++t) sb[t] = *e.slope(l - 1, g0 + 4 * (cc + 1) + t);
     tmem_wait_ld(ra);
     tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
-    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * cc, ra, sa, acc);
-    discard_chunk(e, l - 1, cc);
-    if (cc + 2 < 8) {
+    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * cc, ra, sa, acc, gate);
+    discard_chunk(e, l - 1, cbase + 32 * cc);
+    if (cc + 2 < 4) {
 #pragma unroll
-      for (int t = 0; t < 4; ++t) sa[t] = *e.slope(l - 1, 4 * (cc + 2) + t);
+      for (int t = 0; t < 4; ++t) sa[t] = *e.slope(l - 1, g0 + 4 * (cc + 2) + t);
     }
     tmem_wait_ld(rb);
-    if (cc + 2 < 8) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
-    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * (cc + 1), rb, sb, acc);
-    discard_chunk(e, l - 1, cc + 1);
+    if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
+    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * (cc + 1), rb, sb, acc, gate);
+    discard_chunk(e, l - 1, cbase + 32 * (cc + 1));
   }
 }
 
@@ -617,9 +653,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t bar0 = smem_u32(smem + kOffBar);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
-  const uint32_t a_ready = bar0 + 8u * (2 * kStages);
-  const uint32_t d_full = a_ready + 8u;
-  const uint32_t mma_done = d_full + 8u;
+  const uint32_t a_lo = bar0 + 8u * (2 * kStages);   // A columns 0..255 written (epilogue -> MMA)
+  const uint32_t a_hi = a_lo + 8u;                    // A columns 256..511 written
+  const uint32_t d0_full = a_hi + 8u;                 // column half 0 of the product in TMEM
+  const uint32_t d1_full = d0_full + 8u;              // column half 1
+  const uint32_t lo_free = d1_full + 8u;              // (half 1, K 0..255) products have read A
+  const uint32_t mma_done = lo_free + 8u;
   const uint32_t x_full = mma_done + 8u;    // column-half 1 has published its partial sums
   const uint32_t x_empty = x_full + 8u;     // column-half 0 has consumed them
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + kOffTmemSlot);
@@ -636,8 +675,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), kCluster);   // freed when every CTA of the cluster consumed it
     }
-    mbar_init(a_ready, kEpiWarps);
-    mbar_init(d_full, 1);
+    mbar_init(a_lo, kEpiWarps);
+    mbar_init(a_hi, kEpiWarps);
+    mbar_init(d0_full, 1);
+    mbar_init(d1_full, 1);
+    mbar_init(lo_free, 1);
     mbar_init(mma_done, 1);
     mbar_init(x_full, kEpiWarps / 2);
     mbar_init(x_empty, kEpiWarps / 2);
@@ -716,14 +758,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int64_t it = 0; ok && it < iters; ++it) {
         for (int li = 0; ok && li < G; ++li) {
-          if (!mbar_wait(a_ready, a_phase, budget, abort_flag)) {
-            fail();
-            ok = false;
-            break;
-          }
-          a_phase ^= 1u;
-          tc_fence_after();
           for (int ld = 0; ld < kLoadsPerLayer; ++ld) {
+            // (half 0, K 0..255) needs A's columns 0..255, (half 0, K 256..511)
+            // its columns 256..511 (and TMEM half 1 read by the epilogue)
+            if (ld == 0 || ld == kW / kKAtom / 2) {
+              if (!mbar_wait(ld == 0 ? a_lo : a_hi, a_phase, budget, abort_flag)) {
+                fail();
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+            }
             if (!mbar_wait(full_bar(stage), phase, budget, abort_flag)) {
               fail();
               ok = false;
@@ -741,8 +786,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             mma_commit_mc(empty_bar(stage), cmask);
             if (++stage == kStages) stage = 0, phase ^= 1u;
+            if (ld == kW / kKAtom - 1) mma_commit(d0_full);
+            else if (ld == kW / kKAtom + kW / kKAtom / 2 - 1) mma_commit(lo_free);
           }
-          if (ok) mma_commit(d_full);
+          if (!ok) break;
+          a_phase ^= 1u;
+          mma_commit(d1_full);
         }
       }
       // drain: no product may still be writing TMEM when it is freed
@@ -753,13 +802,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue warps ----------------
     const int q = warp & 3;                  // TMEM lane quarter
-    const int ch = (warp - 2) >> 2;          // column half
+    const int ch = (warp - 2) >> 2;          // first or last 128 columns of each half
     const int r = 32 * q + lane;             // row of the tile = TMEM lane
     const int skip = prm.skip;
     Epi e;
     e.A = A;
     e.slab = reinterpret_cast<uint8_t *>(prm.scratch) +
-             (size_t)blockIdx.x * (size_t)(L - 1) * 2 * 32 * kM * 16;
+             (size_t)blockIdx.x * (size_t)(L - 1) * kW * kM * 2;
     e.t_row = tmem + ((uint32_t)(32 * q) << 16);
     e.r = r;
     e.ch = ch;
@@ -779,11 +828,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool prefetcher = (warp == 2 && lane == 0);
     uint32_t d_phase = 0, x_phase = 0;
     bool ok = true;
-    auto arrive_a = [&]() {
+    auto arrive = [&](uint32_t bar) {
       fence_proxy_async();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(a_ready);
+      if (lane == 0) mbar_arrive(bar);
+    };
+    // start of column half h of a product: its products are in TMEM; half 0
+    // gets the gate it must pass before it overwrites A's columns 0..255
+    auto begin_half = [&](int h, Gate &gate) -> bool {
+      gate = Gate{lo_free, d_phase, budget, abort_flag, h == 0, true};
+      if (!mbar_wait(h == 0 ? d0_full : d1_full, d_phase, budget, abort_flag)) return false;
+      tc_fence_after();
+      return true;
     };
     for (int64_t it = 0; ok && it < iters; ++it) {
       const int64_t tile = blockIdx.x + it * gridDim.x;
@@ -802,45 +859,59 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- L0 on CUDA cores ----
       if (skip == 1) layer0<kF16, true>(e);
       else layer0<kF16, false>(e);
-      arrive_a();
+      arrive(a_lo);
+      arrive(a_hi);
 
       // ---- hidden layers L1 .. L{L-1} (forward) ----
       for (int l = 1; ok && l < L; ++l) {
-        if (!mbar_wait(d_full, d_phase, budget, abort_flag)) { fail(); ok = false; break; }
-        d_phase ^= 1u;
-        tc_fence_after();
         const bool last = (l == L - 1), at = (l == skip), feeds = (l == skip - 1);
-        if (last) {
-          if (at) fwd_layer<kF16, true, true, false>(e, l, acc);
-          else fwd_layer<kF16, true, false, false>(e, l, acc);
-        } else if (at) {
-          fwd_layer<kF16, false, true, false>(e, l, acc);
-        } else if (feeds) {
-          fwd_layer<kF16, false, false, true>(e, l, acc);
-        } else {
-          fwd_layer<kF16, false, false, false>(e, l, acc);
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          Gate gate;
+          if (!begin_half(h, gate)) { fail(); ok = false; break; }
+          if (last) {
+            if (at) fwd_half<kF16, true, true, false>(e, l, h, acc, gate);
+            else fwd_half<kF16, true, false, false>(e, l, h, acc, gate);
+          } else if (at) {
+            fwd_half<kF16, false, true, false>(e, l, h, acc, gate);
+          } else if (feeds) {
+            fwd_half<kF16, false, false, true>(e, l, h, acc, gate);
+          } else {
+            fwd_half<kF16, false, false, false>(e, l, h, acc, gate);
+          }
+          gate.pass();
+          if (!gate.ok) { fail(); ok = false; break; }
+          arrive(h == 0 ? a_lo : a_hi);
         }
-        arrive_a();
+        d_phase ^= 1u;
       }
 
       // ---- Jacobian-transpose chain: layers L-1 .. 1 ----
       for (int l = L - 1; ok && l >= 1; --l) {
         // bring this layer's slopes (128 KB of this CTA) into L2 while its products run
-        if (prefetcher) l2_prefetch_bulk(e.slab + (size_t)(l - 1) * 2 * 32 * kM * 16, 2 * 32 * kM * 16);
-        if (!mbar_wait(d_full, d_phase, budget, abort_flag)) { fail(); ok = false; break; }
-        d_phase ^= 1u;
-        tc_fence_after();
+        if (prefetcher) l2_prefetch_bulk(e.slab + (size_t)(l - 1) * kW * kM * 2, kW * kM * 2);
         const bool at = (l == skip), makes = (l - 1 == skip), to_input = (l == 1);
-        if (to_input) {
-          if (at) bwd_layer<kF16, true, false, true>(e, l, acc);
-          else bwd_layer<kF16, false, false, true>(e, l, acc);
-          tc_fence_before();
-        } else {
-          if (at) bwd_layer<kF16, true, false, false>(e, l, acc);
-          else if (makes) bwd_layer<kF16, false, true, false>(e, l, acc);
-          else bwd_layer<kF16, false, false, false>(e, l, acc);
-          arrive_a();
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          Gate gate;
+          if (!begin_half(h, gate)) { fail(); ok = false; break; }
+          if (to_input) {
+            if (at) bwd_half<kF16, true, false, true>(e, l, h, acc, gate);
+            else bwd_half<kF16, false, false, true>(e, l, h, acc, gate);
+          } else if (at) {
+            bwd_half<kF16, true, false, false>(e, l, h, acc, gate);
+          } else if (makes) {
+            bwd_half<kF16, false, true, false>(e, l, h, acc, gate);
+          } else {
+            bwd_half<kF16, false, false, false>(e, l, h, acc, gate);
+          }
+          gate.pass();
+          if (!gate.ok) { fail(); ok = false; break; }
+          // the last product of the tile feeds no A: the next tile's L0 writes it
+          if (!to_input) arrive(h == 0 ? a_lo : a_hi);
+          else tc_fence_before();
         }
+        d_phase ^= 1u;
       }
       if (!ok) break;
       float gx = acc.gx, gy = acc.gy, gz = acc.gz, fpart = acc.f;
@@ -984,7 +1055,7 @@ int query_tc16_grid(int width, int64_t n, int num_sms) {
 
 size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid) {
   (void)width;
-  return (size_t)grid * (size_t)(n_hidden - 1) * 2 * 32 * kM * 16;
+  return (size_t)grid * (size_t)(n_hidden - 1) * kW * kM * 2;   // 16-bit slopes
 }
 
 template <bool kF16>
