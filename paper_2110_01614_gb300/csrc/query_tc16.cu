@@ -287,17 +287,21 @@ __device__ __forceinline__ void act(float z, float neg_bl2e, float inv_beta, flo
   s = (z >= 0.0f) ? r : u * r;
 }
 
-// Slopes are written once and read once, one tile-time later.  They are
-// stored with an L2 evict-last policy, and each 128-byte line is discarded
-// from L2 after its single read, so dead slopes are never written back to HBM.
-__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+// Slopes are written once and read once, up to a tile-time later; all CTAs
+// together keep about 136 MB of them in flight, more than L2 holds.  They are
+// stored with an L2 evict-first policy so that they, and not the weight
+// panels and biases every CTA re-reads, give way when L2 is full; each
+// 128-byte line is discarded from L2 after its single read, so dead slopes
+// are never written back to HBM.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
   uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
   return pol;
 }
 __device__ __forceinline__ void st_slope(uint4 *dst, uint4 v, uint64_t pol) {
-  (void)pol;
-  *dst = v;   // a plain store: the compiler may schedule loads around it freely
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(dst), "r"(v.x),
+               "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
 }
 __device__ __forceinline__ void l2_discard_line(const void *line) {
   asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(line) : "memory");
@@ -382,7 +386,7 @@ struct Epi {
   const float *wout;    // [W]
   const float *w0;      // [W][3]
   const float *wsk;     // three rows of W: W_s[:, nshort + j]
-  uint64_t pol;         // L2 evict-last policy for slope stores
+  uint64_t pol;         // L2 evict-first policy for slope stores
   int lane;
   ActH2 kh;             // packed-FP16 activation constants
   // slopes of layer l, columns 8g..8g+7 (16 B) of this row
@@ -820,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // W_s[:, nshort + j] (j = 0..2): the skip layer's weights on p, FP32, from
     // the transposed copy (row k = nshort + j holds W_s[n][k] over n)
     e.wsk = skip > 0 ? prm.fwd_t + ((size_t)(skip - 1) * kW + kNShort) * kW : prm.fwd_t;
-    e.pol = l2_evict_last_policy();
+    e.pol = l2_evict_first_policy();
     e.kh.neg_bl2e = __float2half2_rn(-prm.beta * 1.4426950408889634f);
     e.kh.inv_beta = __float2half2_rn(1.0f / prm.beta);
     e.kh.half_beta = __float2half2_rn(0.5f * prm.beta);
