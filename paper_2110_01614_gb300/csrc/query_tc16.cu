@@ -24,22 +24,23 @@
 //   * Eq. 2, the test f < eps and the contact point of Eq. 3 (with the
 //     rigid transform of Sec. 4.2) in the final epilogue; float4 stores.
 //
-// Warp roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
-// TMEM owner, warps 2..9 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31;
-// of each 256-column half of a layer, warps 2..5 take the first 128
-// columns, warps 6..9 the last 128).  Producer, MMA and epilogue hand over
+// Warp roles (384 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
+// TMEM owner, warps 2, 3 idle, warps 4..11 = epilogue (warp w reads TMEM
+// lanes 32*(w%4)..+31; of each 256-column half of a layer, warps 4..7 take
+// the first 128 columns, warps 8..11 the last 128).  Producer, MMA and epilogue hand over
 // through mbarriers; every wait is bounded (QueryParams::wait_budget cycles)
 // and on expiry the kernel records kDevTimeout, drains what it has in flight
 // and returns.
 //
-// Products and epilogues overlap within a tile.  Each product runs as four
-// quarter products in the order (half 0, K 0..255), (half 0, K 256..511),
-// (half 1, K 0..255), (half 1, K 256..511), half h landing in TMEM columns
-// 256h..256h+255.  The epilogue of half 0 starts as soon as its products are
-// done and runs while half 1 is multiplied; it rewrites A's columns 0..255
-// only once the (half 1, K 0..255) products have read them.  The next
-// layer's (half 0, K 0..255) products then start while the epilogue of half 1
-// still runs.
+// Products and epilogues overlap within a tile.  Each product runs as two
+// column halves, half h landing in TMEM columns 256h..256h+255; each half
+// walks the eight 64-column K atoms of A.  The epilogue of half 0 starts as
+// soon as its products are done and runs while half 1 is multiplied; half 1
+// reads atoms 0, 2 first and then 1, 3, and the epilogue rewrites each of
+// those atoms only once they have been read.  The next layer's half 0 starts
+// on atoms 0..3 while the epilogue of half 1 still runs, takes atoms 4 and 6
+// once the epilogue has written its first two chunks of every row, and
+// atoms 5 and 7 last.
 
 #include <cudaTypedefs.h>
 
@@ -63,17 +64,40 @@ constexpr int kABytes = kM * kW * 2;                  // 128 KB activation tile
 constexpr int kAtomBytes = kM * kKAtom * 2;           // 16 KB: one K atom of A
 constexpr int kLoadsPerLayer = (kW / kN) * (kW / kKAtom);   // 16
 constexpr int kEpiWarps = 8;
-constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kEpiWarp0 = 4;              // epilogue = warpgroups 1 and 2
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
+// Register split.  The kernel is launched with kLaunchRegs registers per
+// thread (the most 384 threads can have); warpgroup 0 (producer, MMA issuer,
+// two idle warps) gives registers back down to kCtlRegs and the epilogue
+// warpgroups take them up to kEpiRegs.  The shares must not exceed what the
+// launch holds, or the increase would wait for registers that never come;
+// the host refuses to launch a build whose register count differs.
+constexpr int kLaunchRegs = 168;
+constexpr int kCtlRegs = 40;
+constexpr int kEpiRegs = 232;
+static_assert(128 * kCtlRegs + 32 * kEpiWarps * kEpiRegs <= kThreads * kLaunchRegs,
+              "register split exceeds the registers of the launch");
+static_assert(kThreads * kLaunchRegs <= 65536, "launch registers exceed the SM");
 constexpr float kInvSqrt2 = 0.70710678118654752f;
 
 // shared-memory map (bytes from a 1024-aligned base)
 constexpr int kOffA = 0;
 constexpr int kOffB = kOffA + kABytes;
 constexpr int kOffBar = kOffB + kStages * kStageBytes;
-// barriers: full[kStages], empty[kStages], a_lo, a_hi, d0_full, d1_full,
-// lo_free, mma_done, x_full, x_empty
-constexpr int kNumBars = 2 * kStages + 8;
+// barriers: full[kStages], empty[kStages], a_lo, a_hi_a, a_hi_b, d0_full,
+// d1_full, lo_free_a, lo_free_b, mma_done, x_full, x_empty
+constexpr int kNumBars = 2 * kStages + 10;
+
+// K atom taken at position pos (0..7) of column half nh.  Epilogue thread
+// group g (0, 1) writes atoms 4h + 2g (its first two chunks) and 4h + 2g + 1
+// of a half h, so atoms 4h and 4h + 2 are ready, and may be overwritten,
+// before 4h + 1 and 4h + 3.  Half 0 takes atoms 0..3 (written by the previous
+// epilogue's half 0), then 4, 6, 5, 7; half 1 takes 0, 2, 1, 3 (freeing
+// them for this epilogue's half 0 in that order), then 4..7.
+__device__ __forceinline__ int k_atom(int nh, int pos) {
+  const int sw = (pos & 4) | ((pos & 1) << 1) | ((pos >> 1) & 1);
+  return (nh == 0) == (pos < 4) ? pos : sw;
+}
 constexpr int kOffTmemSlot = kOffBar + 8 * kNumBars;
 constexpr int kOffAbort = kOffTmemSlot + 4;
 constexpr int kOffExch = ((kOffAbort + 4 + 15) / 16) * 16;   // float4 [kM]
@@ -144,7 +168,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity.  Gives up (false) when
 // the budget of clock cycles is spent or another role has aborted.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget,
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget,
                                        volatile int *abort_flag) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
@@ -358,21 +382,37 @@ struct Acc {
   float gx = 0.f, gy = 0.f, gz = 0.f, f = 0.f;
 };
 
-// The wait an epilogue of column half 0 passes before its first write to A:
-// the (half 1, K 0..255) products must have read A's columns 0..255.
+// The waits an epilogue of column half 0 passes before it overwrites A:
+// part 0 (its first two chunks, atoms 0 and 2) once half 1 has read atoms
+// 0 and 2, part 1 (atoms 1 and 3) once half 1 has read those.
 struct Gate {
-  uint32_t bar, parity;
+  uint32_t bar0, bar1, parity;
   long long budget;
   volatile int *abort;
-  bool pending, ok;
-  __device__ __forceinline__ void pass() {
-    if (pending) {
-      pending = false;
-      ok = mbar_wait(bar, parity, budget, abort);
+  bool pending0, pending1, ok;
+  __device__ __forceinline__ void pass(int part) {
+    if (part ? pending1 : pending0) {
+      const uint32_t bar = part ? bar1 : bar0;
+      if (part) pending1 = false;
+      else pending0 = false;
+      ok = (mbar_try_wait(bar, parity) || mbar_wait(bar, parity, budget, abort)) && ok;
       tc_fence_after();
     }
   }
+  __device__ __forceinline__ void pass_all() {
+    pass(0);
+    pass(1);
+  }
 };
+
+// Tell the MMA issuer (barrier `bar`) that this warp's writes to A, and its
+// reads of TMEM, are done.
+__device__ __forceinline__ void epi_arrive(uint32_t bar, int lane) {
+  fence_proxy_async();
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar);
+}
 
 // Per-thread state of an epilogue thread for one tile.
 struct Epi {
@@ -398,11 +438,12 @@ struct Epi {
 constexpr int kNShort = kW - 3;
 
 // One 32-column chunk of a forward epilogue (layers 1 .. L-1).
+// The 16 packed words of the next A operand go to `hw`; the caller stores them.
 template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP>
 __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uint32_t (&raw)[32],
-                                          Acc &acc, Gate &gate) {
+                                          Acc &acc, uint32_t (&hw)[16]) {
   const float *b = e.bias + (size_t)l * kW + c0;
-  uint32_t hw[16], sw[16];
+  uint32_t sw[16];
   if constexpr (!LAST && !FEEDS_SKIP) {
     // activations and slopes in packed FP16; slopes are kept as FP16 in the slab
 #pragma unroll
@@ -439,8 +480,6 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
     for (int t = 0; t < 4; ++t)
       st_slope(e.slope(l, g0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
                e.pol);
-    gate.pass();
-    store_a_chunk(e.A, e.r, c0, hw);
     return;
   }
 #pragma unroll
@@ -487,25 +526,30 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
       st_slope(e.slope(l, g0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
                e.pol);
   }
-  gate.pass();
-  store_a_chunk(e.A, e.r, c0, hw);
 }
 
 // A forward epilogue over the thread's 128 columns of column half h, TMEM
-// loads double-buffered.
+// loads double-buffered; after the first two chunks it arrives on `mid`
+// (when non-zero).
 template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP>
-__device__ __forceinline__ void fwd_half(const Epi &e, int l, int h, Acc &acc, Gate &gate) {
+__device__ __forceinline__ void fwd_half(const Epi &e, int l, int h, Acc &acc, Gate &gate,
+                                         uint32_t mid) {
   uint32_t ra[32], rb[32];
   const int cbase = 256 * h + 128 * e.ch;
   tmem_ld32_async(e.t_row + cbase, ra);
 #pragma unroll 1
   for (int cc = 0; cc < 4; cc += 2) {
+    uint32_t hw[16];
     tmem_wait_ld(ra);
     tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
-    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * cc, ra, acc, gate);
+    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * cc, ra, acc, hw);
+    gate.pass(cc >> 1);
+    store_a_chunk(e.A, e.r, cbase + 32 * cc, hw);
     tmem_wait_ld(rb);
     if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
-    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * (cc + 1), rb, acc, gate);
+    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * (cc + 1), rb, acc, hw);
+    store_a_chunk(e.A, e.r, cbase + 32 * (cc + 1), hw);
+    if (cc == 0 && mid != 0u) epi_arrive(mid, e.lane);
   }
 }
 
@@ -546,10 +590,10 @@ __device__ __forceinline__ void layer0(const Epi &e) {
 }
 
 // One 32-column chunk of a reverse epilogue: delta_{l-1} = slope_{l-1} * g.
+// The 16 packed words of the next A operand go to `dw` (unused for TO_INPUT).
 template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT>
 __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (&raw)[32],
-                                          const uint4 (&sl)[4], Acc &acc, Gate &gate) {
-  uint32_t dw[16];
+                                          const uint4 (&sl)[4], Acc &acc, uint32_t (&dw)[16]) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     float4 s0, s1, s2, w_a, w_b, w_c;
@@ -591,10 +635,6 @@ __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (
     dw[2 * q] = Op<kF16>::pack(dv[0], dv[1]);
     dw[2 * q + 1] = Op<kF16>::pack(dv[2], dv[3]);
   }
-  if (!TO_INPUT) {
-    gate.pass();
-    store_a_chunk(e.A, e.r, c0, dw);
-  }
 }
 
 // After a chunk's slopes have been consumed, drop their L2 lines: the warp's
@@ -612,9 +652,11 @@ __device__ __forceinline__ void discard_chunk(const Epi &e, int l, int c0) {
 
 // A reverse epilogue over the thread's 128 columns of column half h: TMEM
 // loads and the slopes of the next chunk are fetched while the current chunk
-// is processed.
+// is processed; after the first two chunks it arrives on `mid` (when
+// non-zero).
 template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT>
-__device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, Gate &gate) {
+__device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, Gate &gate,
+                                         uint32_t mid) {
   uint32_t ra[32], rb[32];
   uint4 sa[4], sb[4];
   const int cbase = 256 * h + 128 * e.ch;
@@ -626,9 +668,14 @@ __device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, G
   for (int cc = 0; cc < 4; cc += 2) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) sb[t] = *e.slope(l - 1, g0 + 4 * (cc + 1) + t);
+    uint32_t dw[16];
     tmem_wait_ld(ra);
     tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
-    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * cc, ra, sa, acc, gate);
+    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * cc, ra, sa, acc, dw);
+    if (!TO_INPUT) {
+      gate.pass(cc >> 1);
+      store_a_chunk(e.A, e.r, cbase + 32 * cc, dw);
+    }
     discard_chunk(e, l - 1, cbase + 32 * cc);
     if (cc + 2 < 4) {
 #pragma unroll
@@ -636,8 +683,10 @@ __device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, G
     }
     tmem_wait_ld(rb);
     if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
-    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * (cc + 1), rb, sb, acc, gate);
+    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * (cc + 1), rb, sb, acc, dw);
+    if (!TO_INPUT) store_a_chunk(e.A, e.r, cbase + 32 * (cc + 1), dw);
     discard_chunk(e, l - 1, cbase + 32 * (cc + 1));
+    if (cc == 0 && mid != 0u) epi_arrive(mid, e.lane);
   }
 }
 
@@ -657,12 +706,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t bar0 = smem_u32(smem + kOffBar);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
-  const uint32_t a_lo = bar0 + 8u * (2 * kStages);   // A columns 0..255 written (epilogue -> MMA)
-  const uint32_t a_hi = a_lo + 8u;                    // A columns 256..511 written
-  const uint32_t d0_full = a_hi + 8u;                 // column half 0 of the product in TMEM
-  const uint32_t d1_full = d0_full + 8u;              // column half 1
-  const uint32_t lo_free = d1_full + 8u;              // (half 1, K 0..255) products have read A
-  const uint32_t mma_done = lo_free + 8u;
+  // epilogue -> MMA: A atoms 0..3 written (and TMEM half 0 read); atoms 4, 6;
+  // atoms 5, 7 (and TMEM half 1 read)
+  const uint32_t a_lo = bar0 + 8u * (2 * kStages);
+  const uint32_t a_hi_a = a_lo + 8u;
+  const uint32_t a_hi_b = a_hi_a + 8u;
+  // MMA -> epilogue: column half 0 / 1 of the product in TMEM; half 1 has
+  // read A atoms 0, 2 / atoms 1, 3
+  const uint32_t d0_full = a_hi_b + 8u;
+  const uint32_t d1_full = d0_full + 8u;
+  const uint32_t lo_free_a = d1_full + 8u;
+  const uint32_t lo_free_b = lo_free_a + 8u;
+  const uint32_t mma_done = lo_free_b + 8u;
   const uint32_t x_full = mma_done + 8u;    // column-half 1 has published its partial sums
   const uint32_t x_empty = x_full + 8u;     // column-half 0 has consumed them
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + kOffTmemSlot);
@@ -680,10 +735,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(empty_bar(s), kCluster);   // freed when every CTA of the cluster consumed it
     }
     mbar_init(a_lo, kEpiWarps);
-    mbar_init(a_hi, kEpiWarps);
+    mbar_init(a_hi_a, kEpiWarps);
+    mbar_init(a_hi_b, kEpiWarps);
     mbar_init(d0_full, 1);
     mbar_init(d1_full, 1);
-    mbar_init(lo_free, 1);
+    mbar_init(lo_free_a, 1);
+    mbar_init(lo_free_b, 1);
     mbar_init(mma_done, 1);
     mbar_init(x_full, kEpiWarps / 2);
     mbar_init(x_empty, kEpiWarps / 2);
@@ -713,6 +770,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort_flag = 1;
   };
 
+  // every warp ends here: all TMEM traffic is done before the owner frees it,
+  // and no CTA leaves while a cluster peer may still multicast into it.  Each
+  // role calls it from its own register region.
+  auto finish = [&](bool tmem_owner) {
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    if (tmem_owner) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kW));
+    }
+  };
+
+  if (warp < kEpiWarp0) {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kCtlRegs));
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
@@ -733,7 +805,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               ok = false;
               break;
             }
-            const int nh = ld / (kW / kKAtom), kb = ld % (kW / kKAtom);
+            const int nh = ld / (kW / kKAtom), kb = k_atom(nh, ld % (kW / kKAtom));
             if (load_idx != prm.drop_load) {
               mbar_expect_tx(full_bar(stage), kStageBytes);   // all slices land here
               tma_load_2d_mc(sB + stage * kStageBytes + crank * (kSliceRows * kKAtom * 2), map,
@@ -763,10 +835,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t it = 0; ok && it < iters; ++it) {
         for (int li = 0; ok && li < G; ++li) {
           for (int ld = 0; ld < kLoadsPerLayer; ++ld) {
-            // (half 0, K 0..255) needs A's columns 0..255, (half 0, K 256..511)
-            // its columns 256..511 (and TMEM half 1 read by the epilogue)
-            if (ld == 0 || ld == kW / kKAtom / 2) {
-              if (!mbar_wait(ld == 0 ? a_lo : a_hi, a_phase, budget, abort_flag)) {
+            const int nh = ld / (kW / kKAtom), pos = ld % (kW / kKAtom), kb = k_atom(nh, pos);
+            // half 0 needs A atoms 0..3 (and TMEM half 0 read) before it
+            // starts, atoms 4, 6 and then 5, 7 (and TMEM half 1 read) later
+            if (nh == 0 && (pos == 0 || pos == 4 || pos == 6)) {
+              const uint32_t bar = pos == 0 ? a_lo : (pos == 4 ? a_hi_a : a_hi_b);
+              if (!mbar_wait(bar, a_phase, budget, abort_flag)) {
                 fail();
                 ok = false;
                 break;
@@ -779,19 +853,19 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             tc_fence_after();
-            const int nh = ld / (kW / kKAtom), kb = ld % (kW / kKAtom);
             const uint32_t d = tmem + (uint32_t)(nh * kN);
             const uint32_t a_atom = sA + kb * kAtomBytes;
             const uint32_t b_stage = sB + stage * kStageBytes;
 #pragma unroll
             for (int ks = 0; ks < kKAtom / 16; ++ks) {
               mma_16(d, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32),
-                     Op<kF16>::idesc, (kb | ks) != 0 ? 1u : 0u);
+                     Op<kF16>::idesc, (pos | ks) != 0 ? 1u : 0u);
             }
             mma_commit_mc(empty_bar(stage), cmask);
             if (++stage == kStages) stage = 0, phase ^= 1u;
-            if (ld == kW / kKAtom - 1) mma_commit(d0_full);
-            else if (ld == kW / kKAtom + kW / kKAtom / 2 - 1) mma_commit(lo_free);
+            if (nh == 0 && pos == 7) mma_commit(d0_full);
+            else if (nh == 1 && pos == 1) mma_commit(lo_free_a);
+            else if (nh == 1 && pos == 3) mma_commit(lo_free_b);
           }
           if (!ok) break;
           a_phase ^= 1u;
@@ -803,10 +877,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       volatile int no_abort = 0;
       if (!mbar_wait(mma_done, 0, budget, &no_abort)) fail();
     }
+  }
+  finish(warp == 1);
   } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kEpiRegs));
     // ---------------- epilogue warps ----------------
     const int q = warp & 3;                  // TMEM lane quarter
-    const int ch = (warp - 2) >> 2;          // first or last 128 columns of each half
+    const int ch = (warp - kEpiWarp0) >> 2;  // first or last 128 columns of each half
     const int r = 32 * q + lane;             // row of the tile = TMEM lane
     const int skip = prm.skip;
     Epi e;
@@ -829,19 +906,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     e.kh.inv_beta = __float2half2_rn(1.0f / prm.beta);
     e.kh.half_beta = __float2half2_rn(0.5f * prm.beta);
     e.lane = lane;
-    const bool prefetcher = (warp == 2 && lane == 0);
+    const bool prefetcher = (warp == kEpiWarp0 && lane == 0);
     uint32_t d_phase = 0, x_phase = 0;
     bool ok = true;
-    auto arrive = [&](uint32_t bar) {
-      fence_proxy_async();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar);
-    };
+    auto arrive = [&](uint32_t bar) { epi_arrive(bar, lane); };
     // start of column half h of a product: its products are in TMEM; half 0
-    // gets the gate it must pass before it overwrites A's columns 0..255
+    // gets the gates it must pass before it overwrites A's columns 0..255
     auto begin_half = [&](int h, Gate &gate) -> bool {
-      gate = Gate{lo_free, d_phase, budget, abort_flag, h == 0, true};
+      gate = Gate{lo_free_a, lo_free_b, d_phase, budget, abort_flag, h == 0, h == 0, true};
       if (!mbar_wait(h == 0 ? d0_full : d1_full, d_phase, budget, abort_flag)) return false;
       tc_fence_after();
       return true;
@@ -864,7 +936,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (skip == 1) layer0<kF16, true>(e);
       else layer0<kF16, false>(e);
       arrive(a_lo);
-      arrive(a_hi);
+      arrive(a_hi_a);
+      arrive(a_hi_b);
 
       // ---- hidden layers L1 .. L{L-1} (forward) ----
       for (int l = 1; ok && l < L; ++l) {
@@ -873,19 +946,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int h = 0; h < 2; ++h) {
           Gate gate;
           if (!begin_half(h, gate)) { fail(); ok = false; break; }
+          const uint32_t mid = h == 1 ? a_hi_a : 0u;
           if (last) {
-            if (at) fwd_half<kF16, true, true, false>(e, l, h, acc, gate);
-            else fwd_half<kF16, true, false, false>(e, l, h, acc, gate);
+            if (at) fwd_half<kF16, true, true, false>(e, l, h, acc, gate, mid);
+            else fwd_half<kF16, true, false, false>(e, l, h, acc, gate, mid);
           } else if (at) {
-            fwd_half<kF16, false, true, false>(e, l, h, acc, gate);
+            fwd_half<kF16, false, true, false>(e, l, h, acc, gate, mid);
           } else if (feeds) {
-            fwd_half<kF16, false, false, true>(e, l, h, acc, gate);
+            fwd_half<kF16, false, false, true>(e, l, h, acc, gate, mid);
           } else {
-            fwd_half<kF16, false, false, false>(e, l, h, acc, gate);
+            fwd_half<kF16, false, false, false>(e, l, h, acc, gate, mid);
           }
-          gate.pass();
+          gate.pass_all();
           if (!gate.ok) { fail(); ok = false; break; }
-          arrive(h == 0 ? a_lo : a_hi);
+          arrive(h == 0 ? a_lo : a_hi_b);
         }
         d_phase ^= 1u;
       }
@@ -899,20 +973,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int h = 0; h < 2; ++h) {
           Gate gate;
           if (!begin_half(h, gate)) { fail(); ok = false; break; }
+          const uint32_t mid = h == 1 ? a_hi_a : 0u;
           if (to_input) {
-            if (at) bwd_half<kF16, true, false, true>(e, l, h, acc, gate);
-            else bwd_half<kF16, false, false, true>(e, l, h, acc, gate);
+            if (at) bwd_half<kF16, true, false, true>(e, l, h, acc, gate, 0u);
+            else bwd_half<kF16, false, false, true>(e, l, h, acc, gate, 0u);
           } else if (at) {
-            bwd_half<kF16, true, false, false>(e, l, h, acc, gate);
+            bwd_half<kF16, true, false, false>(e, l, h, acc, gate, mid);
           } else if (makes) {
-            bwd_half<kF16, false, true, false>(e, l, h, acc, gate);
+            bwd_half<kF16, false, true, false>(e, l, h, acc, gate, mid);
           } else {
-            bwd_half<kF16, false, false, false>(e, l, h, acc, gate);
+            bwd_half<kF16, false, false, false>(e, l, h, acc, gate, mid);
           }
-          gate.pass();
+          gate.pass_all();
           if (!gate.ok) { fail(); ok = false; break; }
           // the last product of the tile feeds no A: the next tile's L0 writes it
-          if (!to_input) arrive(h == 0 ? a_lo : a_hi);
+          if (!to_input) arrive(h == 0 ? a_lo : a_hi_b);
           else tc_fence_before();
         }
         d_phase ^= 1u;
@@ -963,14 +1038,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  cluster_sync();      // no CTA leaves while a peer may still multicast into it
-  if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kW));
+    finish(false);
   }
 }
 
@@ -1064,8 +1132,13 @@ size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid) {
 
 template <bool kF16>
 cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(query_tc16_kernel<kF16>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  // the register split inside the kernel is only valid for this count
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, query_tc16_kernel<kF16>);
+  if (e != cudaSuccess) return e;
+  if (fa.numRegs != kLaunchRegs) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(query_tc16_kernel<kF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kSmemBytes);
   if (e != cudaSuccess) return e;
   const int grid = query_tc16_grid(p.width, p.n, num_sms);
   cudaLaunchConfig_t cfg = {};
