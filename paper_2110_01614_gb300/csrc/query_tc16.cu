@@ -53,7 +53,13 @@ constexpr int kW = 512;                    // network width handled here
 constexpr int kM = 128;                    // points per tile (MMA M, TMEM lanes)
 constexpr int kN = 256;                    // MMA N (one half of a layer)
 constexpr int kKAtom = 64;                 // K elements per 128-byte swizzle atom
-constexpr int kStages = 3;
+// Weight-panel ring depth.  Two stages leave room for the small FP32 weights
+// below; the epilogue, not the weight stream, bounds the kernel.
+constexpr int kStages = 2;
+// The biases of the first kMaxHidden layers, W_0, the skip layer's weights on
+// p and w_out stay in shared memory (30 KB, FP32); deeper layers read their
+// biases from global memory.
+constexpr int kMaxHidden = 8;
 // CTAs per cluster sharing every weight panel: each CTA fetches 1/kCluster of
 // the panel's rows and the TMA multicasts it into all of them, so L2 streams
 // each panel once per cluster instead of once per CTA.
@@ -83,7 +89,11 @@ constexpr float kInvSqrt2 = 0.70710678118654752f;
 // shared-memory map (bytes from a 1024-aligned base)
 constexpr int kOffA = 0;
 constexpr int kOffB = kOffA + kABytes;
-constexpr int kOffBar = kOffB + kStages * kStageBytes;
+constexpr int kOffBias = kOffB + kStages * kStageBytes;   // float [kMaxHidden][kW]
+constexpr int kOffW0 = kOffBias + kMaxHidden * kW * 4;     // float [kW][3]
+constexpr int kOffWsk = kOffW0 + kW * 3 * 4;               // float [3][kW]: W_s[:, kW - 3 + j]
+constexpr int kOffWout = kOffWsk + 3 * kW * 4;             // float [kW]
+constexpr int kOffBar = kOffWout + kW * 4;
 // barriers: full[kStages], empty[kStages], a_lo, a_hi_a, a_hi_b, d0_full,
 // d1_full, lo_free_a, lo_free_b, mma_done, x_full, x_empty
 constexpr int kNumBars = 2 * kStages + 10;
@@ -367,8 +377,18 @@ __device__ __forceinline__ void act_h2(float z0, float z1, const ActH2 &k, __hal
 }
 __device__ __forceinline__ uint32_t h2_bits(__half2 v) { return *reinterpret_cast<uint32_t *>(&v); }
 
-__device__ __forceinline__ float4 ldg4(const float *p) {
-  return __ldg(reinterpret_cast<const float4 *>(p));
+// The kernel's dynamic shared memory (same base as the kernel's own view).
+extern __shared__ __align__(1024) uint8_t g_smem[];
+
+// Floats idx..idx+3 of the small-weight array at byte offset `off` of shared
+// memory (a plain load: the compiler may schedule it freely).
+__device__ __forceinline__ float4 lds4(int off, int idx) {
+  return *reinterpret_cast<const float4 *>(g_smem + off + 4 * idx);
+}
+// Bias floats idx..idx+3 of layer l (idx counts from layer 0).
+__device__ __forceinline__ float4 bias4(const float *gbias, int l, int idx) {
+  return l < kMaxHidden ? lds4(kOffBias, idx)
+                        : __ldg(reinterpret_cast<const float4 *>(gbias + idx));
 }
 __device__ __forceinline__ float comp(const float4 &v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
@@ -422,10 +442,7 @@ struct Epi {
   int r, ch;            // tile row (= TMEM lane); which 128 columns of each half
   float neg_bl2e, inv_beta;
   float px, py, pz;     // query point in the body frame
-  const float *bias;    // [n_hidden][W]
-  const float *wout;    // [W]
-  const float *w0;      // [W][3]
-  const float *wsk;     // three rows of W: W_s[:, nshort + j]
+  const float *gbias;   // [n_hidden][W] biases in global memory
   uint64_t pol;         // L2 evict-first policy for slope stores
   int lane;
   ActH2 kh;             // packed-FP16 activation constants
@@ -442,18 +459,18 @@ constexpr int kNShort = kW - 3;
 template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP>
 __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uint32_t (&raw)[32],
                                           Acc &acc, uint32_t (&hw)[16]) {
-  const float *b = e.bias + (size_t)l * kW + c0;
+  const int b = l * kW + c0;     // bias index
   uint32_t sw[16];
   if constexpr (!LAST && !FEEDS_SKIP) {
     // activations and slopes in packed FP16; slopes are kept as FP16 in the slab
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const float4 bq = ldg4(b + 4 * q);
+      const float4 bq = bias4(e.gbias, l, b + 4 * q);
       float4 s0, s1, s2;
       if (AT_SKIP) {
-        s0 = ldg4(e.wsk + c0 + 4 * q);
-        s1 = ldg4(e.wsk + kW + c0 + 4 * q);
-        s2 = ldg4(e.wsk + 2 * kW + c0 + 4 * q);
+        s0 = lds4(kOffWsk, c0 + 4 * q);
+        s1 = lds4(kOffWsk, kW + c0 + 4 * q);
+        s2 = lds4(kOffWsk, 2 * kW + c0 + 4 * q);
       }
       float z[4];
 #pragma unroll
@@ -484,13 +501,13 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const float4 bq = ldg4(b + 4 * q);
+    const float4 bq = bias4(e.gbias, l, b + 4 * q);
     float4 wq = make_float4(0.f, 0.f, 0.f, 0.f), s0, s1, s2;
-    if (LAST) wq = ldg4(e.wout + c0 + 4 * q);
+    if (LAST) wq = lds4(kOffWout, c0 + 4 * q);
     if (AT_SKIP) {
-      s0 = ldg4(e.wsk + c0 + 4 * q);
-      s1 = ldg4(e.wsk + kW + c0 + 4 * q);
-      s2 = ldg4(e.wsk + 2 * kW + c0 + 4 * q);
+      s0 = lds4(kOffWsk, c0 + 4 * q);
+      s1 = lds4(kOffWsk, kW + c0 + 4 * q);
+      s2 = lds4(kOffWsk, 2 * kW + c0 + 4 * q);
     }
     float hv[4], sv[4];
 #pragma unroll
@@ -562,10 +579,10 @@ __device__ __forceinline__ void layer0(const Epi &e) {
     uint32_t hw[16], sw[16];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const float4 bq = ldg4(e.bias + c0 + 4 * q);
-      const float4 w_a = ldg4(e.w0 + 3 * (c0 + 4 * q));       // 12 weights of 4 columns
-      const float4 w_b = ldg4(e.w0 + 3 * (c0 + 4 * q) + 4);
-      const float4 w_c = ldg4(e.w0 + 3 * (c0 + 4 * q) + 8);
+      const float4 bq = lds4(kOffBias, c0 + 4 * q);
+      const float4 w_a = lds4(kOffW0, 3 * (c0 + 4 * q));       // 12 weights of 4 columns
+      const float4 w_b = lds4(kOffW0, 3 * (c0 + 4 * q) + 4);
+      const float4 w_c = lds4(kOffW0, 3 * (c0 + 4 * q) + 8);
       const float w[12] = {w_a.x, w_a.y, w_a.z, w_a.w, w_b.x, w_b.y,
                            w_b.z, w_b.w, w_c.x, w_c.y, w_c.z, w_c.w};
       float hv[4], sv[4];
@@ -598,14 +615,14 @@ __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (
   for (int q = 0; q < 8; ++q) {
     float4 s0, s1, s2, w_a, w_b, w_c;
     if (MAKES_SKIP_DELTA) {
-      s0 = ldg4(e.wsk + c0 + 4 * q);
-      s1 = ldg4(e.wsk + kW + c0 + 4 * q);
-      s2 = ldg4(e.wsk + 2 * kW + c0 + 4 * q);
+      s0 = lds4(kOffWsk, c0 + 4 * q);
+      s1 = lds4(kOffWsk, kW + c0 + 4 * q);
+      s2 = lds4(kOffWsk, 2 * kW + c0 + 4 * q);
     }
     if (TO_INPUT) {
-      w_a = ldg4(e.w0 + 3 * (c0 + 4 * q));
-      w_b = ldg4(e.w0 + 3 * (c0 + 4 * q) + 4);
-      w_c = ldg4(e.w0 + 3 * (c0 + 4 * q) + 8);
+      w_a = lds4(kOffW0, 3 * (c0 + 4 * q));
+      w_b = lds4(kOffW0, 3 * (c0 + 4 * q) + 4);
+      w_c = lds4(kOffW0, 3 * (c0 + 4 * q) + 8);
     }
     const uint32_t swords[2] = {comp_u(sl[q >> 1], 2 * (q & 1)), comp_u(sl[q >> 1], 2 * (q & 1) + 1)};
     const float2 sa = Op<true>::unpack(swords[0]);     // slopes are FP16 in the slab
@@ -747,6 +764,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     fence_proxy_async();
+  }
+  {
+    // the small FP32 weights, once per CTA
+    float4 *dst = reinterpret_cast<float4 *>(smem + kOffBias);
+    const float4 *bsrc = reinterpret_cast<const float4 *>(prm.bias);
+    const int nb = (L < kMaxHidden ? L : kMaxHidden) * kW / 4;
+    for (int i = threadIdx.x; i < nb; i += kThreads) dst[i] = __ldg(bsrc + i);
+    dst = reinterpret_cast<float4 *>(smem + kOffW0);
+    const float4 *w0src = reinterpret_cast<const float4 *>(prm.w0);
+    for (int i = threadIdx.x; i < kW * 3 / 4; i += kThreads) dst[i] = __ldg(w0src + i);
+    // W_s[:, nshort + j] (j = 0..2): the skip layer's weights on p, from the
+    // transposed copy (row k = nshort + j holds W_s[n][k] over n)
+    dst = reinterpret_cast<float4 *>(smem + kOffWsk);
+    const float4 *wssrc = reinterpret_cast<const float4 *>(
+        prm.fwd_t + ((size_t)(prm.skip > 0 ? prm.skip - 1 : 0) * kW + (kW - 3)) * kW);
+    for (int i = threadIdx.x; i < 3 * kW / 4; i += kThreads)
+      dst[i] = prm.skip > 0 ? __ldg(wssrc + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    dst = reinterpret_cast<float4 *>(smem + kOffWout);
+    const float4 *wosrc = reinterpret_cast<const float4 *>(prm.wout);
+    for (int i = threadIdx.x; i < kW / 4; i += kThreads) dst[i] = __ldg(wosrc + i);
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -895,12 +932,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     e.ch = ch;
     e.neg_bl2e = -prm.beta * 1.4426950408889634f;
     e.inv_beta = 1.0f / prm.beta;
-    e.bias = prm.bias;
-    e.wout = prm.wout;
-    e.w0 = prm.w0;
-    // W_s[:, nshort + j] (j = 0..2): the skip layer's weights on p, FP32, from
-    // the transposed copy (row k = nshort + j holds W_s[n][k] over n)
-    e.wsk = skip > 0 ? prm.fwd_t + ((size_t)(skip - 1) * kW + kNShort) * kW : prm.fwd_t;
+    e.gbias = prm.bias;
     e.pol = l2_evict_first_policy();
     e.kh.neg_bl2e = __float2half2_rn(-prm.beta * 1.4426950408889634f);
     e.kh.inv_beta = __float2half2_rn(1.0f / prm.beta);
@@ -1076,7 +1108,7 @@ bool query_tc16_supported(int width, int n_hidden, int skip) {
 }
 
 bool make_tc16_tmaps(NetDevice &net, int width, int n_hidden, bool fp16) {
-  if (width != kW || n_hidden < 2) return false;
+  if (!query_tc16_supported(width, n_hidden, 0)) return false;
   const int rows = (n_hidden - 1) * kW;
   return encode_panel_map(&net.tmap_fwd, net.fwd16, rows, fp16) &&
          encode_panel_map(&net.tmap_bwd, net.bwd16, rows, fp16);
