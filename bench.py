@@ -46,8 +46,8 @@ FLOP_PER_QUERY = 2 * MAC_PER_QUERY
 # SHA-256 of the kernel source it was taken on; reported only while the
 # source is unchanged.
 TRAFFIC_CAPTURE = {
-    "source_sha256": "e32f0553d07b5b8898b11be6faa6f41363eec2a2f2049a1e5cd469707acbc18e",
-    "bytes_per_launch": 2.910098e9 + 3.495056e9,
+    "source_sha256": "7203aac45c55c8ef1fe12c76bbfd783aa0e9b6aaf255dab89bf21f8513d417bf",
+    "bytes_per_launch": 3.862205e9 + 4.801872e9,
 }
 
 
