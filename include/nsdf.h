@@ -189,6 +189,24 @@ nsdf_status nsdf_query_grouped(nsdf_ctx *ctx, const float *pts,
                                float *out_n_sdf, nsdf_stream stream);
 
 /*
+ * nsdf_query_grouped for a scene of posed bodies (Sec. 4.2 per body): body k
+ * is placed by the rigid transform T[16k .. 16k+15], a row-major 4x4 in
+ * DEVICE memory (float, 4-byte aligned; the last row is not read).  Its
+ * points are queried at T_k^{-1} p and its normals rotated by T_k[:3,:3], as
+ * in nsdf_collide.  The poses are read (and inverted, in FP64, on the device)
+ * by every call, so a captured CUDA graph replays with updated poses.  A
+ * singular T_k is replaced by the identity and reported by nsdf_sync_status
+ * as NSDF_ERR_INVALID_ARG.  Other arguments and errors as nsdf_query_grouped;
+ * T == NULL is NSDF_ERR_INVALID_ARG.  This batching form has no counterpart
+ * in the paper, which places one body.
+ */
+nsdf_status nsdf_query_grouped_T(nsdf_ctx *ctx, const float *pts,
+                                 const int64_t *offsets, const int64_t *counts,
+                                 int64_t max_total, float eps, const float *T,
+                                 float *out_pts, float *out_n_sdf,
+                                 nsdf_stream stream);
+
+/*
  * Autotuner of the grouped launch: times every tile shape (4 or 8 points per
  * thread) and every CTAs-per-SM count that fits on this exact problem
  * (3 timed launches each, CUDA events), keeps the fastest in the context for

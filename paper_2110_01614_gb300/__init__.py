@@ -23,7 +23,7 @@ __all__ = [
     "NsdfError", "NSDF_FP32", "NSDF_BF16", "NSDF_FP16", "NSDF_RAW_GRADIENT", "make_arch",
     "nsdf_num_params", "nsdf_create", "nsdf_destroy", "nsdf_load_weights",
     "nsdf_query", "nsdf_collide", "nsdf_collide_noalloc", "nsdf_backward", "nsdf_query_grouped",
-    "nsdf_autotune_grouped", "nsdf_set_grouped_config",
+    "nsdf_query_grouped_T",
     "nsdf_autotune_grouped", "nsdf_set_grouped_config",
     "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status", "nsdf_debug_inject",
     "nsdf_status_string", "NeuralSDF", "library",
@@ -143,6 +143,14 @@ def nsdf_query_grouped(ctx, pts, offsets, counts, max_total, eps, out_pts, out_n
     _check(library().nsdf_query_grouped(ctx, _ptr(pts), _ptr(offsets), _ptr(counts),
                                         int(max_total), float(eps), _ptr(out_pts),
                                         _ptr(out_n_sdf), _stream(stream)), "nsdf_query_grouped")
+
+
+def nsdf_query_grouped_T(ctx, pts, offsets, counts, max_total, eps, T, out_pts, out_n_sdf=None,
+                         stream=None):
+    """nsdf_query_grouped with a device [n_nets, 4, 4] tensor of body poses."""
+    _check(library().nsdf_query_grouped_T(ctx, _ptr(pts), _ptr(offsets), _ptr(counts),
+                                          int(max_total), float(eps), _ptr(T), _ptr(out_pts),
+                                          _ptr(out_n_sdf), _stream(stream)), "nsdf_query_grouped_T")
 
 
 def nsdf_autotune_grouped(ctx, pts, offsets, counts, max_total, eps, out_pts, out_n_sdf=None,

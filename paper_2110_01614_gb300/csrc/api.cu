@@ -162,6 +162,7 @@ struct nsdf_ctx {
   // grouped launches: device table of per-network pointers, work list, tuned shape
   NetPtrs *d_netptrs = nullptr;
   int32_t *d_tile_start = nullptr;
+  float *d_body = nullptr;     // [n_nets][kBodyFloats] poses of nsdf_query_grouped_T
   int grouped_pt = 8;          // points per thread of the FP32 tile (4 or 8)
   int grouped_cps = 0;         // CTAs per SM (0: as many as fit)
 };
@@ -418,6 +419,7 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
   if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_err, 4);
   if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_netptrs, (size_t)n_nets);
   if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_tile_start, (size_t)n_nets + 1);
+  if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_body, (size_t)n_nets * kBodyFloats);
   if (st == NSDF_OK) {
     std::vector<NetPtrs> h(n_nets);
     for (int k = 0; k < n_nets; ++k) {
@@ -629,6 +631,7 @@ struct GroupedArgs {
   int64_t max_total;
   float eps;
   float *out_pts, *out_n_sdf;
+  const float *T = nullptr;   // device [n_nets][16] poses, or none
 };
 
 nsdf_status grouped_check(nsdf_ctx *ctx, const GroupedArgs &g) {
@@ -665,6 +668,10 @@ nsdf_status grouped_launch(nsdf_ctx *ctx, const GroupedArgs &g, int pt, int cps,
                                          fp32_tile_points(a.width, pt), g.max_total,
                                          ctx->d_tile_start, ctx->d_err, s);
   if (e != cudaSuccess) return map_err(e);
+  if (g.T) {
+    e = launch_body_transforms(g.T, ctx->n_nets, ctx->d_body, ctx->d_err, s);
+    if (e != cudaSuccess) return map_err(e);
+  }
   QueryParams p{};
   fill_net(ctx, 0, p);
   p.pts = reinterpret_cast<const float4 *>(g.pts);
@@ -679,6 +686,7 @@ nsdf_status grouped_launch(nsdf_ctx *ctx, const GroupedArgs &g, int pt, int cps,
   p.g_counts = g.counts;
   p.g_tile_start = ctx->d_tile_start;
   p.g_netptrs = ctx->d_netptrs;
+  p.g_T = g.T ? ctx->d_body : nullptr;
   return map_err(launch_query_fp32_grouped(p, pt, grid, s));
 }
 
@@ -690,6 +698,19 @@ nsdf_status nsdf_query_grouped(nsdf_ctx *ctx, const float *pts, const int64_t *o
   const GroupedArgs g{pts, offsets, counts, max_total, eps, out_pts, out_n_sdf};
   nsdf_status st = grouped_check(ctx, g);
   if (st != NSDF_OK || max_total == 0) return st;
+  return grouped_launch(ctx, g, ctx->grouped_pt, ctx->grouped_cps,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+nsdf_status nsdf_query_grouped_T(nsdf_ctx *ctx, const float *pts, const int64_t *offsets,
+                                 const int64_t *counts, int64_t max_total, float eps,
+                                 const float *T, float *out_pts, float *out_n_sdf,
+                                 nsdf_stream stream) {
+  GroupedArgs g{pts, offsets, counts, max_total, eps, out_pts, out_n_sdf};
+  g.T = T;
+  nsdf_status st = grouped_check(ctx, g);
+  if (st != NSDF_OK || max_total == 0) return st;
+  if (!T || (reinterpret_cast<uintptr_t>(T) & 3u)) return NSDF_ERR_INVALID_ARG;
   return grouped_launch(ctx, g, ctx->grouped_pt, ctx->grouped_cps,
                         reinterpret_cast<cudaStream_t>(stream));
 }

@@ -80,7 +80,13 @@ struct QueryParams {
   const int64_t *g_offsets, *g_counts;
   const int32_t *g_tile_start;   // [g_nets + 1], built on the device
   const NetPtrs *g_netptrs;      // [g_nets]
+  // grouped: per-network rigid pose, kBodyFloats floats each (T^{-1} rows
+  // 0..2, then T[:3,:3]); nullable (no transform)
+  const float *g_T;
 };
+
+// Floats per network in QueryParams::g_T.
+constexpr int kBodyFloats = 24;
 
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_query_fp32(const QueryParams &p, int num_sms, cudaStream_t s);
@@ -109,6 +115,9 @@ nsdf_status ctx_set_transform(const float *T, QueryParams *p);
 
 cudaError_t launch_build_tile_list(const int64_t *offsets, const int64_t *counts, int n_nets, int P,
                                    int64_t max_total, int32_t *tile_start, int *err,
+                                   cudaStream_t s);
+// T [n_nets][16] (row-major 4x4 poses, device) -> out [n_nets][kBodyFloats]
+cudaError_t launch_body_transforms(const float *T, int n_nets, float *out, int *err,
                                    cudaStream_t s);
 
 size_t backward_smem_bytes(int width, int n_hidden, int64_t n_params);

@@ -153,6 +153,8 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
     int64_t base, nvalid;
     const float *w0 = prm.w0, *bias = prm.bias, *fwd_t = prm.fwd_t, *bwdw = prm.bwd,
                 *wout = prm.wout, *bout = prm.bout;
+    // the tile's pose (Sec. 4.2): T^{-1} rows 0..2 and T[:3,:3], or none
+    const float *Ti = prm.has_T ? prm.Ti : nullptr, *Rn = prm.R;
     if (grouped) {
       int lo = 0, hi = prm.g_nets;               // last k with tile_start[k] <= tile
       while (hi - lo > 1) {
@@ -164,6 +166,10 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
       nvalid = prm.g_counts[lo] - local * C::P;
       const NetPtrs &np = prm.g_netptrs[lo];
       w0 = np.w0; bias = np.bias; fwd_t = np.fwd_t; bwdw = np.bwd; wout = np.wout; bout = np.bout;
+      if (prm.g_T) {
+        Ti = prm.g_T + (size_t)kBodyFloats * lo;
+        Rn = Ti + 12;
+      }
     } else {
       base = tile * C::P;
       nvalid = prm.n - base;
@@ -174,8 +180,8 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
       int64_t idx = base + tid;
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
       if (tid < nvalid) p = prm.pts[idx];
-      if (prm.has_T) {
-        const float *t = prm.Ti;
+      if (Ti) {
+        const float *t = Ti;
         float x = t[0] * p.x + t[1] * p.y + t[2] * p.z + t[3];
         float y = t[4] * p.x + t[5] * p.y + t[6] * p.z + t[7];
         float z = t[8] * p.x + t[9] * p.y + t[10] * p.z + t[11];
@@ -335,8 +341,8 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
           if (prm.raw_gradient) { nx = gx; ny = gy; nz = gz; }
           prm.out_n_sdf[idx] = make_float4(nx, ny, nz, f);
         } else {
-          if (prm.has_T) {
-            const float *R = prm.R;
+          if (Ti) {
+            const float *R = Rn;
             float wx = R[0] * nx + R[1] * ny + R[2] * nz;
             float wy = R[3] * nx + R[4] * ny + R[5] * nz;
             float wz = R[6] * nx + R[7] * ny + R[8] * nz;

@@ -6,7 +6,7 @@
 * penalty: gradient of sum max(0, eps - f)^2 with respect to 1,048,576 vertices.
 * grouped: 16 networks of the 3-64-64-64-1 shape with log-uniform counts in
   [2k, 400k] (about 1.2M points) in one grouped launch, autotuned, replayed
-  from a CUDA graph.
+  from a CUDA graph; also with a rigid pose per body (nsdf_query_grouped_T).
 * cloth: 1024 x 1024 cloth, per-step time of Verlet + collision solve for the
   body-scale network in BF16 / FP16 / FP32, and of the exact brute-force mesh
   SDF of every vertex (20,480 triangles) as the plain reference.
@@ -24,7 +24,7 @@ import torch
 
 import synth
 
-from . import (NSDF_BF16, NSDF_FP16, NSDF_FP32, NeuralSDF, nsdf_query_grouped,
+from . import (NSDF_BF16, NSDF_FP16, NSDF_FP32, NeuralSDF, nsdf_query_grouped, nsdf_query_grouped_T,
                nsdf_sync_status)
 from .cloth_sim import ClothSim, mesh_reference_step_ms
 from .fit import MeshFit, penalty_gradient
@@ -84,11 +84,21 @@ def bench_grouped(reps=20):
     with torch.cuda.graph(g, stream=s):
         nsdf_query_grouped(net.ctx, P, O, C, total, 0.002, out, ns)
     ms = events_ms(g.replay, reps)
+    # the same scene with every body placed by its own rigid pose (device array)
+    Tdev = torch.from_numpy(synth.rigid_transforms(16, seed=77)).cuda()
+    with torch.cuda.stream(s):
+        nsdf_query_grouped_T(net.ctx, P, O, C, total, 0.002, Tdev, out, ns)
+    s.synchronize()
+    gT = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gT, stream=s):
+        nsdf_query_grouped_T(net.ctx, P, O, C, total, 0.002, Tdev, out, ns)
+    ms_T = events_ms(gT.replay, reps)
     nsdf_sync_status(net.ctx)
     net.close()
     return {"workload": "grouped", "nets": 16, "points": total, "ms": ms,
-            "queries_per_s": total / (ms * 1e-3), "tile_points_per_thread": pt, "ctas_per_sm": cps,
-            "precision": "fp32"}
+            "queries_per_s": total / (ms * 1e-3), "posed_ms": ms_T,
+            "posed_queries_per_s": total / (ms_T * 1e-3), "tile_points_per_thread": pt,
+            "ctas_per_sm": cps, "precision": "fp32"}
 
 
 def bench_cloth(steps=20):

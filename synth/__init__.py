@@ -20,11 +20,12 @@ from .mesh import icosphere, displaced_icosphere, box_mesh, value_noise
 from .cloth import cloth_grid, spring_list
 from .counts import grouped_counts
 from .training import training_points
+from .poses import rigid_transforms
 
 __all__ = [
     "Stream", "splitmix64", "Arch", "geometric_init", "layer_shapes",
     "n_params", "unpack", "uniform_cube", "ellipsoid_shell",
     "body_scale_points", "uniform_cube_points", "icosphere",
     "displaced_icosphere", "box_mesh", "value_noise", "cloth_grid",
-    "spring_list", "grouped_counts", "training_points",
+    "spring_list", "grouped_counts", "training_points", "rigid_transforms",
 ]

@@ -170,3 +170,97 @@ def test_bad_work_entry_is_reported_not_executed(nsdf):
     assert e.value.status == 1
     assert float(out[25:].min()) == 3.0 and float(out[10:25].min()) == 3.0   # untouched
     net.close()
+
+
+def posed_reference(blobs, offs, counts, pts, T):
+    """FP64 oracle per body with its pose."""
+    f = np.empty(len(pts))
+    N = np.empty((len(pts), 3))
+    x = np.empty((len(pts), 3))
+    for k, b in enumerate(blobs):
+        sl = slice(offs[k], offs[k] + counts[k])
+        if counts[k] == 0:
+            continue
+        f[sl], N[sl], _, x[sl] = mlp.collide(b, TINY, pts[sl], EPS, T=T[k])
+    return f, N, x
+
+
+def test_posed_scene_matches_oracle_and_single_body_path(nsdf):
+    from parity import normal_angle
+    counts = np.array([700, 0, 1500, 64, 2500, 333, 1, 900], dtype=np.int64)
+    offs, total, pts = make_problem(counts, seed=21)
+    net, blobs = grouped_setup(nsdf, n_nets=8)
+    T = synth.rigid_transforms(8, seed=5)
+    P = torch.from_numpy(pts).cuda()
+    out = torch.full_like(P, -7.0)
+    ns = torch.full_like(P, -7.0)
+    nsdf.nsdf_query_grouped_T(net.ctx, P, torch.from_numpy(offs).cuda(),
+                              torch.from_numpy(counts).cuda(), total, EPS,
+                              torch.from_numpy(T).cuda(), out, ns)
+    nsdf.nsdf_sync_status(net.ctx)
+    out, ns = out.cpu().numpy(), ns.cpu().numpy()
+    f, N, x = posed_reference(blobs, offs, counts, pts, T)
+    assert np.abs(ns[:, 3] - f).max() <= 1e-5
+    ok = np.linalg.norm(N, axis=1) > 0
+    assert normal_angle(N[ok], ns[ok, :3]).max() <= 1e-4
+    np.testing.assert_allclose(out[:, :3], x, atol=2e-5)
+    np.testing.assert_array_equal(out[:, 3], pts[:, 3])          # w rides along
+    # the single-body path with the same pose (its inverse is taken on the host)
+    for k in (0, 4):
+        s = nsdf.NeuralSDF(TINY, nsdf.NSDF_FP32).load(blobs[k])
+        d = torch.from_numpy(pts[offs[k]: offs[k] + counts[k]].copy()).cuda()
+        o, n_ = torch.empty_like(d), torch.empty_like(d)
+        s.collide(d, EPS, T=T[k], out_pts=o, out_n_sdf=n_)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(ns[offs[k]: offs[k] + counts[k]], n_.cpu().numpy(), atol=1e-6)
+        s.close()
+    net.close()
+
+
+def test_posed_scene_graph_replays_with_new_poses(nsdf):
+    counts = np.array([3000, 2000, 4000], dtype=np.int64)
+    offs, total, pts = make_problem(counts, seed=22)
+    net, blobs = grouped_setup(nsdf, n_nets=3)
+    P = torch.from_numpy(pts).cuda()
+    O, C = torch.from_numpy(offs).cuda(), torch.from_numpy(counts).cuda()
+    Tdev = torch.from_numpy(synth.rigid_transforms(3, seed=6)).cuda()
+    out, ns = torch.zeros_like(P), torch.zeros_like(P)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        nsdf.nsdf_query_grouped_T(net.ctx, P, O, C, total, EPS, Tdev, out, ns)   # warm-up
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        nsdf.nsdf_query_grouped_T(net.ctx, P, O, C, total, EPS, Tdev, out, ns)
+    for seed in (7, 8):
+        T = synth.rigid_transforms(3, seed=seed)
+        Tdev.copy_(torch.from_numpy(T))
+        ns.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        f, N, x = posed_reference(blobs, offs, counts, pts, T)
+        assert np.abs(ns.cpu().numpy()[:, 3] - f).max() <= 1e-5
+    nsdf.nsdf_sync_status(net.ctx)
+    net.close()
+
+
+def test_posed_scene_rejects_missing_and_singular_poses(nsdf):
+    counts = np.array([100, 50], dtype=np.int64)
+    offs, total, pts = make_problem(counts, seed=23)
+    net, blobs = grouped_setup(nsdf, n_nets=2)
+    P = torch.from_numpy(pts).cuda()
+    O, C = torch.from_numpy(offs).cuda(), torch.from_numpy(counts).cuda()
+    out = torch.empty_like(P)
+    with pytest.raises(nsdf.NsdfError) as e:
+        nsdf.nsdf_query_grouped_T(net.ctx, P, O, C, total, EPS, None, out)
+    assert e.value.status == 1
+    T = synth.rigid_transforms(2, seed=9)
+    T[1, :3, :3] = 0.0                                     # singular pose of body 1
+    nsdf.nsdf_query_grouped_T(net.ctx, P, O, C, total, EPS, torch.from_numpy(T).cuda(), out)
+    with pytest.raises(nsdf.NsdfError) as e:
+        nsdf.nsdf_sync_status(net.ctx)
+    assert e.value.status == 1
+    # body 0 is still answered with its own pose
+    f, N, hit, x = mlp.collide(blobs[0], TINY, pts[:100], EPS, T=T[0])
+    np.testing.assert_allclose(out.cpu().numpy()[:100, :3], x, atol=2e-5)
+    net.close()

@@ -77,3 +77,16 @@ def test_counts_and_cloth():
     assert P.shape == (64, 4)
     np.testing.assert_allclose(P[1, 0] - P[0, 0], 2.0 / 7, rtol=1e-6)
     assert synth.spring_list(8).shape[0] == 2 * 8 * 7 + 2 * 7 * 7
+
+
+def test_rigid_transforms_are_rigid_and_seeded():
+    T = synth.rigid_transforms(64, seed=3)
+    assert T.shape == (64, 4, 4) and T.dtype == np.float32
+    R = T[:, :3, :3].astype(np.float64)
+    np.testing.assert_allclose(np.einsum("nij,nkj->nik", R, R), np.broadcast_to(np.eye(3), R.shape),
+                               atol=1e-6)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-6)
+    np.testing.assert_array_equal(T[:, 3], np.broadcast_to([0, 0, 0, 1], (64, 4)))
+    assert np.abs(T[:, :3, 3]).max() <= 0.5
+    np.testing.assert_array_equal(T, synth.rigid_transforms(64, seed=3))
+    assert not np.array_equal(T, synth.rigid_transforms(64, seed=4))
