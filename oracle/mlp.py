@@ -19,13 +19,22 @@ Definitions followed:
 * Sec. 4.2: for a body placed by a rigid transform T (4x4), the query uses
   p' = T^{-1} p and the normal is rotated back by T[:3, :3].
 
+* Sec. 4.3 (the paper's own networks): a Fourier-feature input layer
+  gamma(p) = [sin(2 pi B p), cos(2 pi B p)] (Tancik et al. 2020; B [m x 3]
+  stored in the blob, sines first) followed by ReLU layers.  Its gradient
+  multiplies g_gamma = W_0^T delta_0 by the feature Jacobian:
+  d sin(2 pi b.p)/dp = 2 pi cos(2 pi b.p) b, d cos(2 pi b.p)/dp =
+  -2 pi sin(2 pi b.p) b.  The ReLU slope is 1 where z > 0 and 0 elsewhere
+  (at z = 0 the gradient is taken as 0, as TensorFlow does; Sec. 4.3 notes
+  that no gradient flows through a ReLU that outputs 0).
+
 Degenerate gradient: when ||grad f|| < 1e-20 the normal is the zero vector,
 so a collided vertex is not moved.
 """
 
 import numpy as np
 
-from synth.weights import unpack
+from synth.weights import ff_matrix, unpack
 
 SQRT2 = np.sqrt(2.0)
 DEGENERATE_NORM = 1e-20
@@ -46,8 +55,27 @@ def _layers(blob, arch):
     return unpack(blob, arch, dtype=np.float64)
 
 
-def _layer_input(l, h, p, arch):
+def activation(z, arch):
+    """softplus_beta (Eq. 1 networks of this build) or ReLU (Sec. 4.3)."""
+    return np.maximum(z, 0.0) if arch.activation == "relu" else softplus(z, arch.beta)
+
+
+def slope(z, arch):
+    """Derivative of the activation: sigmoid(beta z), or the ReLU step (0 at 0)."""
+    return (z > 0.0).astype(np.float64) if arch.activation == "relu" else sigmoid(arch.beta * z)
+
+
+def fourier_features(blob, arch, p):
+    """gamma(p) = [sin(2 pi B p), cos(2 pi B p)] [n, 2m], and the phases 2 pi B p."""
+    B = ff_matrix(blob, arch)
+    phase = 2.0 * np.pi * (p @ B.T)
+    return np.concatenate([np.sin(phase), np.cos(phase)], axis=1), phase
+
+
+def _layer_input(l, h, p, arch, blob=None):
     if l == 0:
+        if arch.ff_freqs > 0:
+            return fourier_features(blob, arch, p)[0]
         return p
     if arch.skip_layer > 0 and l == arch.skip_layer:
         return np.concatenate([h, p], axis=1) / SQRT2
@@ -66,11 +94,11 @@ def forward(blob, arch, p):
     h = p
     for l in range(arch.n_hidden):
         W, b = layers[l]
-        x = _layer_input(l, h, p, arch)
+        x = _layer_input(l, h, p, arch, blob)
         z = x @ W.T + b
         xs.append(x)
         zs.append(z)
-        h = softplus(z, arch.beta)
+        h = activation(z, arch)
     W, b = layers[arch.n_hidden]
     f = (h @ W.T + b)[:, 0]
     return f, zs, xs
@@ -88,9 +116,16 @@ def gradient(blob, arch, p, zs=None):
     direct = np.zeros((n, 3))
     for l in range(arch.n_hidden - 1, -1, -1):
         W, _ = layers[l]
-        delta = sigmoid(arch.beta * zs[l]) * g
+        delta = slope(zs[l], arch) * g
         u = delta @ W
         if l == 0:
+            if arch.ff_freqs > 0:
+                # u = g_gamma; chain through the feature Jacobian
+                m = arch.ff_freqs
+                B = ff_matrix(blob, arch)
+                _, phase = fourier_features(blob, arch, p)
+                coef = u[:, :m] * np.cos(phase) - u[:, m:] * np.sin(phase)
+                return 2.0 * np.pi * (coef @ B) + direct
             return u + direct
         if arch.skip_layer > 0 and l == arch.skip_layer:
             k = W.shape[1] - 3

@@ -13,7 +13,7 @@ Arm hosts.
 """
 
 from .rng import Stream, splitmix64
-from .weights import Arch, geometric_init, layer_shapes, n_params, unpack
+from .weights import Arch, geometric_init, layer_shapes, n_params, unpack, ff_matrix, fourier_relu_init
 from .points import (uniform_cube, ellipsoid_shell, body_scale_points,
                      uniform_cube_points)
 from .mesh import icosphere, displaced_icosphere, box_mesh, value_noise
@@ -23,7 +23,8 @@ from .training import training_points
 from .poses import rigid_transforms
 
 __all__ = [
-    "Stream", "splitmix64", "Arch", "geometric_init", "layer_shapes",
+    "Stream", "splitmix64", "Arch", "geometric_init", "layer_shapes", "ff_matrix",
+    "fourier_relu_init",
     "n_params", "unpack", "uniform_cube", "ellipsoid_shell",
     "body_scale_points", "uniform_cube_points", "icosphere",
     "displaced_icosphere", "box_mesh", "value_noise", "cloth_grid",

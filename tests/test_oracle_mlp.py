@@ -317,3 +317,80 @@ def test_geometric_init_is_a_rough_sphere():
         r = np.linalg.norm(p, axis=1)
         assert np.corrcoef(r, f)[0, 1] > 0.75
         assert f.min() < 0 < f.max()
+
+
+# ---- Fourier-feature ReLU networks (the paper's own architecture, Sec. 4.3) ----
+
+RELU = synth.Arch(3, 32, 3, -1, 100.0, "relu", 0)
+FFR = synth.Arch(3, 32, 3, -1, 100.0, "relu", 16)
+
+
+def _with_B(blob, arch, B):
+    b = blob.copy()
+    b[: arch.ff_freqs * 3] = np.asarray(B, dtype=np.float32).ravel()
+    return b
+
+
+def test_bias_free_relu_network_is_homogeneous_and_satisfies_euler():
+    """Zero biases make a ReLU network positively homogeneous of degree 1:
+    f(a p) = a f(p) for a > 0, and by Euler's theorem grad f(p) . p = f(p).
+    Softplus in place of ReLU, or a wrong slope, breaks both."""
+    blob = synth.fourier_relu_init(RELU, 3)           # all biases are zero
+    p = synth.uniform_cube(200, 4)[:, :3].astype(np.float64)
+    f, _, _ = mlp.forward(blob, RELU, p)
+    for a in (0.5, 2.0, 3.7):
+        fa, _, _ = mlp.forward(blob, RELU, a * p)
+        np.testing.assert_allclose(fa, a * f, rtol=1e-12, atol=1e-12)
+    g = mlp.gradient(blob, RELU, p)
+    np.testing.assert_allclose(np.einsum("ij,ij->i", g, p), f, rtol=1e-10, atol=1e-12)
+
+
+def test_fourier_features_are_periodic_for_integer_frequencies():
+    """With B integer, gamma(p + e_k) = gamma(p), so f and grad f are
+    1-periodic in every coordinate; a missing 2 pi or a mixed-up feature
+    breaks the period."""
+    s = synth.Stream(5)
+    B = np.round(s.normal(16 * 3, std=2.0)).reshape(16, 3)
+    blob = _with_B(synth.fourier_relu_init(FFR, 6), FFR, B)
+    p = synth.uniform_cube(100, 7)[:, :3].astype(np.float64) * 0.4
+    f, g = mlp.query(blob, FFR, p, raw_gradient=True)
+    for k in range(3):
+        q = p.copy()
+        q[:, k] += 1.0
+        fq, gq = mlp.query(blob, FFR, q, raw_gradient=True)
+        np.testing.assert_allclose(fq, f, atol=1e-10)
+        np.testing.assert_allclose(gq, g, atol=1e-8)
+
+
+def test_fourier_relu_gradient_matches_central_differences():
+    """The chain through the feature Jacobian against central differences of
+    the forward pass, at points with every pre-activation away from the
+    ReLU kink (the difference step never crosses one)."""
+    blob = synth.fourier_relu_init(FFR, 8)
+    p = synth.uniform_cube(400, 9)[:, :3].astype(np.float64)
+    f, zs, _ = mlp.forward(blob, FFR, p)
+    margin = np.min([np.abs(z).min(axis=1) for z in zs], axis=0)
+    p = p[margin > 1e-4]
+    assert len(p) > 20
+    g = mlp.gradient(blob, FFR, p)
+    h = 1e-7
+    fd = np.stack([(mlp.forward(blob, FFR, p + h * e)[0] - mlp.forward(blob, FFR, p - h * e)[0]) / (2 * h)
+                   for e in np.eye(3)], axis=1)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-6 * np.abs(g).max())
+
+
+def test_zero_frequencies_give_a_constant_field():
+    """B = 0: gamma(p) = [0 ... 0, 1 ... 1] for every p, so f is constant and
+    grad f vanishes."""
+    blob = _with_B(synth.fourier_relu_init(FFR, 10), FFR, np.zeros((16, 3)))
+    p = synth.uniform_cube(50, 11)[:, :3].astype(np.float64)
+    f, g = mlp.query(blob, FFR, p, raw_gradient=True)
+    np.testing.assert_allclose(f, f[0], atol=1e-14)
+    assert np.abs(g).max() == 0.0
+
+
+def test_relu_slope_is_zero_at_the_kink():
+    """The reading of the ReLU derivative at z = 0: no gradient flows."""
+    z = np.array([[-1.0, 0.0, 2.0]])
+    np.testing.assert_array_equal(mlp.slope(z, RELU), [[0.0, 0.0, 1.0]])
+    np.testing.assert_array_equal(mlp.activation(z, RELU), [[0.0, 0.0, 2.0]])
