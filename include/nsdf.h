@@ -63,12 +63,22 @@ typedef enum {
                      weights must stay within FP16 range (|x| < 65504)         */
 } nsdf_precision;
 
+/* Hidden-layer activation (nsdf_arch.activation). */
+typedef enum {
+  NSDF_ACT_SOFTPLUS = 0, /* softplus_beta(z) = log(1 + exp(beta z)) / beta */
+  NSDF_ACT_RELU = 1      /* max(z, 0); its slope is taken as 0 at z = 0     */
+} nsdf_activation;
+
 /*
- * Network shape (Eq. 1): n_hidden softplus layers L0..L{n_hidden-1} of
- * `width` units, then a linear output unit.  With skip_layer = s > 0,
- * layer L{s-1} has width - in_dim units and L{s} reads [h_{s-1}, p] / sqrt(2).
- * in_dim must be 3; beta > 0 is the softplus sharpness
- * softplus(z) = log(1 + exp(beta z)) / beta.
+ * Network shape (Eq. 1): n_hidden layers L0..L{n_hidden-1} of `width` units
+ * with the activation `activation`, then a linear output unit.  With
+ * skip_layer = s > 0, layer L{s-1} has width - in_dim units and L{s} reads
+ * [h_{s-1}, p] / sqrt(2).  in_dim must be 3; beta > 0 is the softplus
+ * sharpness (ignored by ReLU).  ff_freqs = m > 0 puts the Fourier-feature
+ * layer of the paper's networks (Sec. 4.3) in front: L0 reads
+ * gamma(p) = [sin(2 pi B p), cos(2 pi B p)] (2m values, sines first), with
+ * the frequency matrix B [m x 3] stored at the start of the weight blob;
+ * this needs 2m == width and no skip layer.
  */
 typedef struct {
   int in_dim;
@@ -76,14 +86,17 @@ typedef struct {
   int n_hidden;
   int skip_layer; /* -1: no skip */
   float beta;
+  int activation; /* nsdf_activation */
+  int ff_freqs;   /* 0: the network reads p itself */
 } nsdf_arch;
 
 /* nsdf_query flag: return grad f instead of the unit normal. */
 #define NSDF_RAW_GRADIENT 1u
 
 /*
- * Number of floats in a packed weight blob for `arch`: for each layer in
- * order, W row-major [out x in] then b[out].  Returns 0 for an invalid arch.
+ * Number of floats in a packed weight blob for `arch`: B [ff_freqs x 3]
+ * (when ff_freqs > 0), then for each layer in order, W row-major [out x in]
+ * then b[out].  Returns 0 for an invalid arch.
  */
 size_t nsdf_num_params(const nsdf_arch *arch);
 
@@ -91,7 +104,10 @@ size_t nsdf_num_params(const nsdf_arch *arch);
  * Create a context for n_nets networks of the same shape on the current
  * device.  Synchronous.  Fails with NSDF_ERR_UNSUPPORTED when no kernel of
  * this build handles (arch, prec): FP32 takes widths 32, 64, 128, 256 and
- * 512; BF16 and FP16 take width 512 with at least two hidden layers.
+ * 512 with either activation and Fourier features; BF16 and FP16 take
+ * softplus networks of width 512 with at least two hidden layers and no
+ * Fourier features (a ReLU slope is a 0/1 decision on the sign of z, which
+ * 16-bit pre-activations would flip for many points).
  */
 nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets,
                         nsdf_ctx **out);

@@ -17,10 +17,12 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (NSDF_BF16, NSDF_FP16, NSDF_FP32, NSDF_RAW_GRADIENT, nsdf_arch)
+from ._abi import (NSDF_ACT_RELU, NSDF_ACT_SOFTPLUS, NSDF_BF16, NSDF_FP16, NSDF_FP32,
+                   NSDF_RAW_GRADIENT, nsdf_arch)
 
 __all__ = [
-    "NsdfError", "NSDF_FP32", "NSDF_BF16", "NSDF_FP16", "NSDF_RAW_GRADIENT", "make_arch",
+    "NsdfError", "NSDF_FP32", "NSDF_BF16", "NSDF_FP16", "NSDF_RAW_GRADIENT", "NSDF_ACT_SOFTPLUS",
+    "NSDF_ACT_RELU", "make_arch",
     "nsdf_num_params", "nsdf_create", "nsdf_destroy", "nsdf_load_weights",
     "nsdf_query", "nsdf_collide", "nsdf_collide_noalloc", "nsdf_backward", "nsdf_query_grouped",
     "nsdf_query_grouped_T",
@@ -65,14 +67,17 @@ def _stream(stream):
     return int(stream)
 
 
-def make_arch(width, n_hidden, skip_layer=-1, beta=100.0, in_dim=3):
-    return nsdf_arch(in_dim, width, n_hidden, skip_layer, beta)
+def make_arch(width, n_hidden, skip_layer=-1, beta=100.0, in_dim=3, activation="softplus",
+              ff_freqs=0):
+    return nsdf_arch(in_dim, width, n_hidden, skip_layer, beta,
+                     NSDF_ACT_RELU if activation == "relu" else NSDF_ACT_SOFTPLUS, ff_freqs)
 
 
 def _arch(a):
     if isinstance(a, nsdf_arch):
         return a
-    return nsdf_arch(a.in_dim, a.width, a.n_hidden, a.skip_layer, a.beta)
+    return make_arch(a.width, a.n_hidden, a.skip_layer, a.beta, a.in_dim,
+                     getattr(a, "activation", "softplus"), getattr(a, "ff_freqs", 0))
 
 
 def nsdf_status_string(status):

@@ -30,7 +30,12 @@ NSDF_RAW_GRADIENT = 1
 class nsdf_arch(ctypes.Structure):
     _fields_ = [("in_dim", ctypes.c_int), ("width", ctypes.c_int),
                 ("n_hidden", ctypes.c_int), ("skip_layer", ctypes.c_int),
-                ("beta", ctypes.c_float)]
+                ("beta", ctypes.c_float), ("activation", ctypes.c_int),
+                ("ff_freqs", ctypes.c_int)]
+
+
+NSDF_ACT_SOFTPLUS = 0
+NSDF_ACT_RELU = 1
 
 
 _P = ctypes.c_void_p

@@ -26,6 +26,9 @@ bool arch_valid(const nsdf_arch *a) {
   if (a->in_dim != 3 || a->width < 4 || a->n_hidden < 1 || a->n_hidden > kMaxLayers - 1) return false;
   if (!(a->beta > 0.0f) || !std::isfinite(a->beta)) return false;
   if (a->skip_layer != -1 && (a->skip_layer < 1 || a->skip_layer >= a->n_hidden)) return false;
+  if (a->activation != NSDF_ACT_SOFTPLUS && a->activation != NSDF_ACT_RELU) return false;
+  if (a->ff_freqs < 0) return false;
+  if (a->ff_freqs > 0 && (2 * a->ff_freqs != a->width || a->skip_layer != -1)) return false;
   return true;
 }
 
@@ -34,7 +37,10 @@ int layer_out(const nsdf_arch &a, int l) {
   if (a.skip_layer > 0 && l == a.skip_layer - 1) return a.width - a.in_dim;
   return a.width;
 }
-int layer_in(const nsdf_arch &a, int l) { return l == 0 ? a.in_dim : a.width; }
+int layer_in(const nsdf_arch &a, int l) {
+  if (l > 0) return a.width;
+  return a.ff_freqs > 0 ? 2 * a.ff_freqs : a.in_dim;
+}
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -76,6 +82,7 @@ bool invert4x4(const double *m, double *inv) {
 
 struct PackPlan {
   int width, n_hidden, skip;
+  int ff;   // m, frequencies [m][3] at the start of the blob
   int64_t woff[kMaxLayers];
   int64_t boff[kMaxLayers];
   int out[kMaxLayers];
@@ -83,6 +90,7 @@ struct PackPlan {
 
 struct PackTargets {
   float *w0, *bias, *fwd_t, *bwd, *wout, *bout;
+  float *ffB, *ff0_t, *ff0;
   uint16_t *fwd16, *bwd16;
   int fp16;   // 16-bit copies as FP16 (1) or BF16 (0)
 };
@@ -102,9 +110,20 @@ __global__ void pack_weights_kernel(const float *__restrict__ blob, PackPlan pla
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // L0 weights and all hidden biases, output layer
-  for (int64_t t = t0; t < (int64_t)W * 3; t += stride) {
-    const int n = (int)(t / 3), k = (int)(t % 3);
-    net.w0[t] = n < plan.out[0] ? blob[plan.woff[0] + (int64_t)n * 3 + k] : 0.0f;
+  if (plan.ff > 0) {
+    // B, then L0 (width x 2m = width x width) as two panels
+    for (int64_t t = t0; t < (int64_t)plan.ff * 3; t += stride) net.ffB[t] = blob[t];
+    const float *W0 = blob + plan.woff[0];
+    for (int64_t t = t0; t < (int64_t)W * W; t += stride) {
+      const int r = (int)(t / W), c = (int)(t % W);
+      net.ff0_t[t] = W0[(int64_t)c * W + r];   // [k=r][n=c] = W_0[n][k]
+      net.ff0[t] = W0[t];                      // [n=r][k=c] = W_0[n][k]
+    }
+  } else {
+    for (int64_t t = t0; t < (int64_t)W * 3; t += stride) {
+      const int n = (int)(t / 3), k = (int)(t % 3);
+      net.w0[t] = n < plan.out[0] ? blob[plan.woff[0] + (int64_t)n * 3 + k] : 0.0f;
+    }
   }
   for (int64_t t = t0; t < (int64_t)L * W; t += stride) {
     const int l = (int)(t / W), n = (int)(t % W);
@@ -193,7 +212,7 @@ bool use_bf16(const nsdf_ctx *ctx) { return ctx->prec == NSDF_BF16 || ctx->prec 
 
 int query_grid(const nsdf_ctx *ctx, int64_t n) {
   if (use_bf16(ctx)) return query_tc16_grid(ctx->arch.width, n, ctx->num_sms);
-  return query_fp32_grid(ctx->arch.width, n, ctx->num_sms);
+  return query_fp32_grid(ctx->arch.width, n, ctx->num_sms, ctx->arch.ff_freqs > 0);
 }
 
 size_t query_scratch(const nsdf_ctx *ctx, int grid) {
@@ -220,10 +239,13 @@ void fill_net(const nsdf_ctx *ctx, int net, QueryParams &p) {
   const NetDevice &d = ctx->nets[net];
   p.w0 = d.w0; p.bias = d.bias; p.fwd_t = d.fwd_t; p.bwd = d.bwd; p.wout = d.wout; p.bout = d.bout;
   p.fwd16 = d.fwd16; p.bwd16 = d.bwd16;
+  p.ffB = d.ffB; p.ff0_t = d.ff0_t; p.ff0 = d.ff0;
   p.width = ctx->arch.width;
   p.n_hidden = ctx->arch.n_hidden;
   p.skip = ctx->arch.skip_layer;
   p.beta = ctx->arch.beta;
+  p.relu = ctx->arch.activation == NSDF_ACT_RELU ? 1 : 0;
+  p.ff = ctx->arch.ff_freqs;
   p.err = ctx->d_err;
   p.wait_budget = ctx->wait_budget;
   p.drop_load = ctx->drop_load;
@@ -359,7 +381,7 @@ extern "C" {
 
 size_t nsdf_num_params(const nsdf_arch *arch) {
   if (!arch_valid(arch)) return 0;
-  size_t total = 0;
+  size_t total = (size_t)arch->ff_freqs * arch->in_dim;
   for (int l = 0; l <= arch->n_hidden; ++l)
     total += (size_t)layer_out(*arch, l) * layer_in(*arch, l) + layer_out(*arch, l);
   return total;
@@ -386,7 +408,9 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
   if (!arch_valid(arch) || n_nets < 1 || n_nets > 4096) return NSDF_ERR_INVALID_ARG;
   if (prec != NSDF_FP32 && prec != NSDF_BF16 && prec != NSDF_FP16) return NSDF_ERR_INVALID_ARG;
   if (prec == NSDF_FP32 && !query_fp32_supported(arch->width)) return NSDF_ERR_UNSUPPORTED;
-  if (prec != NSDF_FP32 && !query_tc16_supported(arch->width, arch->n_hidden, arch->skip_layer))
+  if (prec != NSDF_FP32 &&
+      (arch->activation != NSDF_ACT_SOFTPLUS || arch->ff_freqs > 0 ||
+       !query_tc16_supported(arch->width, arch->n_hidden, arch->skip_layer)))
     return NSDF_ERR_UNSUPPORTED;
   nsdf_ctx *ctx = new (std::nothrow) nsdf_ctx;
   if (!ctx) return NSDF_ERR_OOM;
@@ -411,6 +435,11 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
     if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd, hid);
     if (st == NSDF_OK) st = ctx_alloc(ctx, &d.wout, (size_t)W);
     if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bout, 4);
+    if (st == NSDF_OK && arch->ff_freqs > 0) {
+      st = ctx_alloc(ctx, &d.ffB, (size_t)arch->ff_freqs * 3);
+      if (st == NSDF_OK) st = ctx_alloc(ctx, &d.ff0_t, (size_t)W * W);
+      if (st == NSDF_OK) st = ctx_alloc(ctx, &d.ff0, (size_t)W * W);
+    }
     if (st == NSDF_OK && prec != NSDF_FP32) {
       st = ctx_alloc(ctx, &d.fwd16, hid);
       if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd16, hid);
@@ -424,7 +453,7 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
     std::vector<NetPtrs> h(n_nets);
     for (int k = 0; k < n_nets; ++k) {
       const NetDevice &d = ctx->nets[k];
-      h[k] = NetPtrs{d.w0, d.bias, d.fwd_t, d.bwd, d.wout, d.bout};
+      h[k] = NetPtrs{d.w0, d.bias, d.fwd_t, d.bwd, d.wout, d.bout, d.ffB, d.ff0_t, d.ff0};
     }
     st = map_err(cudaMemcpy(ctx->d_netptrs, h.data(), sizeof(NetPtrs) * n_nets,
                             cudaMemcpyHostToDevice));
@@ -479,7 +508,8 @@ nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w, size_t n_f
   plan.width = a.width;
   plan.n_hidden = a.n_hidden;
   plan.skip = a.skip_layer;
-  int64_t off = 0;
+  plan.ff = a.ff_freqs;
+  int64_t off = (int64_t)a.ff_freqs * a.in_dim;
   for (int l = 0; l <= a.n_hidden; ++l) {
     plan.out[l] = layer_out(a, l);
     plan.woff[l] = off;
@@ -488,8 +518,8 @@ nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w, size_t n_f
     off += layer_out(a, l);
   }
   const NetDevice &d = ctx->nets[net];
-  PackTargets tg{d.w0, d.bias, d.fwd_t, d.bwd, d.wout, d.bout, d.fwd16, d.bwd16,
-                 ctx->prec == NSDF_FP16 ? 1 : 0};
+  PackTargets tg{d.w0,    d.bias,  d.fwd_t, d.bwd,   d.wout,  d.bout, d.ffB,
+                 d.ff0_t, d.ff0,   d.fwd16, d.bwd16, ctx->prec == NSDF_FP16 ? 1 : 0};
   pack_weights_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(src, plan, tg);
   cudaError_t e = last_err();
   if (tmp) {
@@ -583,13 +613,15 @@ nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n, const floa
     p.n = n;
     p.grad_scale = g_sdf;
     p.out_grad = reinterpret_cast<float4 *>(g_pts);
-    const int grid = query_fp32_grid(a.width, n, ctx->num_sms);
+    const int grid = query_fp32_grid(a.width, n, ctx->num_sms, a.ff_freqs > 0);
     nsdf_status st = ensure_scratch(ctx, query_fp32_scratch_bytes(a.width, a.n_hidden, grid));
     if (st != NSDF_OK) return st;
     p.scratch = ctx->scratch;
     return map_err(launch_query_fp32(p, ctx->num_sms, s));
   }
-  if (!backward_supported(a.width, a.n_hidden, n_params)) return NSDF_ERR_UNSUPPORTED;
+  if (a.activation != NSDF_ACT_SOFTPLUS || a.ff_freqs > 0 ||
+      !backward_supported(a.width, a.n_hidden, n_params))
+    return NSDF_ERR_UNSUPPORTED;
   int64_t woff[65], boff[65];
   int out[65];
   int64_t off = 0;
@@ -652,7 +684,7 @@ nsdf_status grouped_check(nsdf_ctx *ctx, const GroupedArgs &g) {
 // enough CTAs for the largest possible work list, at most what is resident.
 int grouped_grid(const nsdf_ctx *ctx, int pt, int cps, int64_t max_total) {
   const int P = fp32_tile_points(ctx->arch.width, pt);
-  const int fit = fp32_ctas_per_sm(ctx->arch.width, pt);
+  const int fit = fp32_ctas_per_sm(ctx->arch.width, pt, ctx->arch.ff_freqs > 0);
   if (cps <= 0 || cps > fit) cps = fit;
   const int64_t max_tiles = (max_total + P - 1) / P + ctx->n_nets;
   const int64_t cap = (int64_t)ctx->num_sms * cps;
@@ -731,7 +763,7 @@ nsdf_status nsdf_autotune_grouped(nsdf_ctx *ctx, const float *pts, const int64_t
   int best_pt = ctx->grouped_pt, best_cps = ctx->grouped_cps;
   const int pts_opts[2] = {4, 8};
   for (int pt : pts_opts) {
-    const int fit = fp32_ctas_per_sm(ctx->arch.width, pt);
+    const int fit = fp32_ctas_per_sm(ctx->arch.width, pt, ctx->arch.ff_freqs > 0);
     for (int cps = 1; cps <= fit; ++cps) {
       st = grouped_launch(ctx, g, pt, cps, s);             // warm-up (and scratch growth)
       if (st != NSDF_OK) break;

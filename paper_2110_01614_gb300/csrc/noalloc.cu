@@ -83,7 +83,7 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   const size_t slab = tc16 ? query_tc16_scratch_bytes(width, n_hidden, 1)
                            : query_fp32_scratch_bytes(width, n_hidden, 1);
   const int64_t slabs = (int64_t)(kNoAllocScratchBytes / slab);
-  const int per_sm = tc16 ? 1 : query_fp32_grid(width, (int64_t)1 << 40, 1);
+  const int per_sm = tc16 ? 1 : query_fp32_grid(width, (int64_t)1 << 40, 1, p.ff > 0);
   if (slabs < per_sm || per_sm < 1) return NSDF_ERR_TOO_LARGE;
   if (tc16 && slabs < query_tc16_min_grid()) return NSDF_ERR_TOO_LARGE;
   int64_t sm_arg = slabs / per_sm;

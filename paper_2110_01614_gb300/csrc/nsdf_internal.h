@@ -31,6 +31,11 @@ struct NetDevice {
   float *bwd = nullptr;    // [n_hidden-1][width(n)][width(k)] = W_l[n][k]
   float *wout = nullptr;   // [width]      output weights (zero padded)
   float *bout = nullptr;   // [1]
+  // Fourier-feature networks (ff_freqs = m > 0, 2m = width): B and L0 as
+  // width x width panels in the layouts of fwd_t / bwd
+  float *ffB = nullptr;    // [m][3]
+  float *ff0_t = nullptr;  // [width(k)][width(n)] = W_0[n][k]
+  float *ff0 = nullptr;    // [width(n)][width(k)] = W_0[n][k]
   // 16-bit forms (tensor-core B operands, K-major; BF16 or FP16 bits)
   uint16_t *fwd16 = nullptr;  // [n_hidden-1][width(n)][width(k)] = W_l
   uint16_t *bwd16 = nullptr;  // [n_hidden-1][width(k)][width(n)] = W_l^T
@@ -43,6 +48,7 @@ struct NetDevice {
 // FP32 weight pointers of one network, as a device array for grouped launches.
 struct NetPtrs {
   const float *w0, *bias, *fwd_t, *bwd, *wout, *bout;
+  const float *ffB, *ff0_t, *ff0;
 };
 
 // Everything one fused query launch needs (passed by value).
@@ -63,6 +69,9 @@ struct QueryParams {
   const uint16_t *fwd16, *bwd16;
   int width, n_hidden, skip;
   float beta;
+  int relu;                  // activation: 0 softplus_beta, 1 ReLU
+  int ff;                    // Fourier features: m (0 = none; 2m = width)
+  const float *ffB, *ff0_t, *ff0;
   // per-CTA scratch and the context's error word
   float *scratch;
   int *err;
@@ -91,11 +100,11 @@ constexpr int kBodyFloats = 24;
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_query_fp32(const QueryParams &p, int num_sms, cudaStream_t s);
 size_t query_fp32_scratch_bytes(int width, int n_hidden, int grid);
-int query_fp32_grid(int width, int64_t n, int num_sms);
+int query_fp32_grid(int width, int64_t n, int num_sms, bool ff = false);
 bool query_fp32_supported(int width);
 // grouped FP32 launches with a chosen tile shape (pt = points per thread, 4 or 8)
 int fp32_tile_points(int width, int pt);
-int fp32_ctas_per_sm(int width, int pt);
+int fp32_ctas_per_sm(int width, int pt, bool ff = false);
 size_t fp32_scratch_bytes_pt(int width, int pt, int n_hidden, int grid);
 cudaError_t launch_query_fp32_grouped(const QueryParams &p, int pt, int grid, cudaStream_t s);
 

@@ -11,7 +11,13 @@
   body-scale network in BF16 / FP16 / FP32, and of the exact brute-force mesh
   SDF of every vertex (20,480 triangles) as the plain reference.
 
-Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped cloth]
+* paper_arch: the paper's own network shapes (Sec. 4.3: a Fourier-feature
+  layer of 128 frequencies, then 8 (dragon) or 4 (bunny) ReLU layers of 256
+  units), collision query of 1,048,576 body-scale points in the FP32 kernel;
+  the paper's Table 1 quotes 255 ms / 350 ms for 1M queries on a Tesla T4
+  (context only: other hardware, other weights).
+
+Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped cloth paper_arch]
 """
 
 import json
@@ -118,13 +124,32 @@ def bench_cloth(steps=20):
     return res
 
 
+def bench_paper_arch(reps=10):
+    res = {"workload": "paper_arch", "points": 1 << 20, "precision": "fp32"}
+    pts = torch.from_numpy(synth.body_scale_points(1 << 20, 1)).cuda()
+    out, ns = torch.empty_like(pts), torch.empty_like(pts)
+    for name, L in (("dragon_8x256", 8), ("bunny_4x256", 4)):
+        arch = synth.Arch(3, 256, L, -1, 100.0, "relu", 128)
+        net = NeuralSDF(arch, NSDF_FP32).load(synth.fourier_relu_init(arch, 0))
+        net.collide(pts, 0.002, out_pts=out, out_n_sdf=ns)
+        ms = events_ms(lambda: net.collide(pts, 0.002, out_pts=out, out_n_sdf=ns), reps)
+        nsdf_sync_status(net.ctx)
+        net.close()
+        # algorithmic MAC per query: L0 and L-1 hidden 256x256 products forward,
+        # the same transposed backward (incl. W_0^T), plus the output unit
+        mac = 2 * L * 256 * 256 + 256
+        res[name] = {"ms": ms, "queries_per_s": (1 << 20) / (ms * 1e-3),
+                     "tflops": 2 * mac * (1 << 20) / (ms * 1e-3) / 1e12}
+    return res
+
+
 def main(argv):
-    which = argv or ["fit", "penalty", "grouped", "cloth"]
+    which = argv or ["fit", "penalty", "grouped", "cloth", "paper_arch"]
     torch.cuda.set_device(0)
     for w in which:
         t0 = time.perf_counter()
         r = {"fit": bench_fit, "penalty": bench_penalty, "grouped": bench_grouped,
-             "cloth": bench_cloth}[w]()
+             "cloth": bench_cloth, "paper_arch": bench_paper_arch}[w]()
         r["wall_s"] = time.perf_counter() - t0
         print(json.dumps(r), flush=True)
 
