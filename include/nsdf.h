@@ -187,6 +187,24 @@ nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n,
                           float *g_weights, float *g_pts, nsdf_stream stream);
 
 /*
+ * Gradient of the L1 fitting loss of Sec. 3.1, L = (1/n) sum_i |f(p_i) - d_i|
+ * (training points p_i, float4 [n], w ignored; exact signed distances d_i,
+ * float [n]; both DEVICE), for network 0 of a 16-bit context (tensor cores).
+ * g_weights (device, nsdf_num_params floats, blob layout) is overwritten with
+ * dL/dtheta; loss (device float, nullable) receives L.  The derivative of
+ * |f - d| is taken as sign(f - d), 0 at equality.  The hidden-layer weight
+ * gradients are products over the points of the kernel's 16-bit deltas and
+ * activations with FP32 accumulation (cuBLAS); the other sums are FP32 and
+ * reduced in a fixed order, so repeated calls give identical results.  Uses
+ * about 2 n_hidden x width x 2 bytes of device memory per point, allocated on
+ * the first call and when n grows.  FP32 contexts: NSDF_ERR_UNSUPPORTED (use
+ * nsdf_backward); n = 0: NSDF_ERR_INVALID_ARG.
+ */
+nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n,
+                         const float *targets, float *g_weights, float *loss,
+                         nsdf_stream stream);
+
+/*
  * Many bodies in one launch: network k answers points
  * pts[offsets[k] .. offsets[k] + counts[k]) for k < n_nets of the context,
  * with the collision solve of nsdf_collide (no transform).  offsets and

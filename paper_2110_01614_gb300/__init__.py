@@ -25,7 +25,7 @@ __all__ = [
     "NSDF_ACT_RELU", "make_arch",
     "nsdf_num_params", "nsdf_create", "nsdf_destroy", "nsdf_load_weights",
     "nsdf_query", "nsdf_collide", "nsdf_collide_noalloc", "nsdf_backward", "nsdf_query_grouped",
-    "nsdf_query_grouped_T",
+    "nsdf_query_grouped_T", "nsdf_l1_grad",
     "nsdf_autotune_grouped", "nsdf_set_grouped_config",
     "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status", "nsdf_debug_inject",
     "nsdf_status_string", "NeuralSDF", "library",
@@ -156,6 +156,12 @@ def nsdf_query_grouped_T(ctx, pts, offsets, counts, max_total, eps, T, out_pts, 
     _check(library().nsdf_query_grouped_T(ctx, _ptr(pts), _ptr(offsets), _ptr(counts),
                                           int(max_total), float(eps), _ptr(T), _ptr(out_pts),
                                           _ptr(out_n_sdf), _stream(stream)), "nsdf_query_grouped_T")
+
+
+def nsdf_l1_grad(ctx, pts, targets, g_weights, loss=None, stream=None):
+    """Gradient of mean |f(p) - d| for a 16-bit context (Sec. 3.1 fitting loss)."""
+    _check(library().nsdf_l1_grad(ctx, _ptr(pts), pts.shape[0], _ptr(targets), _ptr(g_weights),
+                                  _ptr(loss), _stream(stream)), "nsdf_l1_grad")
 
 
 def nsdf_autotune_grouped(ctx, pts, offsets, counts, max_total, eps, out_pts, out_n_sdf=None,

@@ -55,6 +55,7 @@ SIGNATURES = {
     "nsdf_backward": (_ST, [_P, _P, _I64, _P, _P, _P, _P, _P]),
     "nsdf_query_grouped": (_ST, [_P, _P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]),
     "nsdf_query_grouped_T": (_ST, [_P, _P, _P, _P, _I64, ctypes.c_float, _P, _P, _P, _P]),
+    "nsdf_l1_grad": (_ST, [_P, _P, _I64, _P, _P, _P, _P]),
     "nsdf_autotune_grouped": (_ST, [_P, _P, _P, _P, _I64, ctypes.c_float, _P, _P, _P,
                                     ctypes.POINTER(ctypes.c_int)]),
     "nsdf_set_grouped_config": (_ST, [_P, ctypes.c_int, ctypes.c_int]),

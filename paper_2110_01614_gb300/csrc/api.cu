@@ -182,6 +182,7 @@ struct nsdf_ctx {
   NetPtrs *d_netptrs = nullptr;
   int32_t *d_tile_start = nullptr;
   float *d_body = nullptr;     // [n_nets][kBodyFloats] poses of nsdf_query_grouped_T
+  void *train = nullptr;       // buffers of nsdf_l1_grad (train.cu)
   int grouped_pt = 8;          // points per thread of the FP32 tile (4 or 8)
   int grouped_cps = 0;         // CTAs per SM (0: as many as fit)
 };
@@ -375,6 +376,27 @@ nsdf_status ctx_query_setup(nsdf_ctx *ctx, QueryParams *p, int *num_sms, int *wi
 
 nsdf_status ctx_set_transform(const float *T, QueryParams *p) { return set_transform(T, *p); }
 
+nsdf_status ctx_query_scratch(nsdf_ctx *ctx, int64_t n, QueryParams *p) {
+  nsdf_status st = ensure_scratch(ctx, query_scratch(ctx, query_grid(ctx, n)));
+  if (st == NSDF_OK) p->scratch = ctx->scratch;
+  return st;
+}
+
+int64_t ctx_blob_offsets(const nsdf_ctx *ctx, int64_t *woff, int64_t *boff, int *out) {
+  const nsdf_arch &a = ctx->arch;
+  int64_t off = (int64_t)a.ff_freqs * a.in_dim;
+  for (int l = 0; l <= a.n_hidden; ++l) {
+    out[l] = layer_out(a, l);
+    woff[l] = off;
+    off += (int64_t)layer_out(a, l) * layer_in(a, l);
+    boff[l] = off;
+    off += layer_out(a, l);
+  }
+  return off;
+}
+
+void **ctx_train_slot(nsdf_ctx *ctx) { return &ctx->train; }
+
 }  // namespace nsdf
 
 extern "C" {
@@ -480,6 +502,7 @@ nsdf_status nsdf_destroy(nsdf_ctx *ctx) {
     if (ctx->ev_done[i]) cudaEventDestroy(ctx->ev_done[i]);
   }
   if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+  train_state_free(ctx->train);
   delete ctx;
   return NSDF_OK;
 }

@@ -89,6 +89,10 @@ struct QueryParams {
   const int64_t *g_offsets, *g_counts;
   const int32_t *g_tile_start;   // [g_nets + 1], built on the device
   const NetPtrs *g_netptrs;      // [g_nets]
+  // training form of the 16-bit kernel (both non-null): every layer's A
+  // operand as [n_hidden][ceil(n / 128) * 128][width] 16-bit values:
+  // save_h[l] = h_l, save_d[l] = delta_l = d f / d z_l
+  uint16_t *save_h, *save_d;
   // grouped: per-network rigid pose, kBodyFloats floats each (T^{-1} rows
   // 0..2, then T[:3,:3]); nullable (no transform)
   const float *g_T;
@@ -121,6 +125,15 @@ int query_tc16_min_grid();   // CTAs of one cluster: the smallest grid of the ke
 nsdf_status ctx_query_setup(nsdf_ctx *ctx, QueryParams *p, int *num_sms, int *width,
                             int *n_hidden, bool *tc16, bool *fp16, const NetDevice **net);
 nsdf_status ctx_set_transform(const float *T, QueryParams *p);
+// Per-CTA scratch of a query over n points (allocated or grown here).
+nsdf_status ctx_query_scratch(nsdf_ctx *ctx, int64_t n, QueryParams *p);
+// Blob offsets of the weights / biases of layers 0..n_hidden and their
+// output counts; returns the blob size.
+int64_t ctx_blob_offsets(const nsdf_ctx *ctx, int64_t *woff, int64_t *boff, int *out);
+// The context's slot for the training state of train.cu (freed by
+// train_state_free in nsdf_destroy).
+void **ctx_train_slot(nsdf_ctx *ctx);
+void train_state_free(void *state);
 
 cudaError_t launch_build_tile_list(const int64_t *offsets, const int64_t *counts, int n_nets, int P,
                                    int64_t max_total, int32_t *tile_start, int *err,

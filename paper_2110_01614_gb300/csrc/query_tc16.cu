@@ -446,6 +446,10 @@ struct Epi {
   uint64_t pol;         // L2 evict-first policy for slope stores
   int lane;
   ActH2 kh;             // packed-FP16 activation constants
+  // save mode (training): every A operand also goes to [n_hidden][n_pad][W]
+  // 16-bit arrays, activations h_l to save_h[l], deltas to save_d[l]
+  uint16_t *save_h, *save_d;
+  int64_t n_pad, row;   // rows of a saved layer; this thread's row in it
   // slopes of layer l, columns 8g..8g+7 (16 B) of this row
   __device__ __forceinline__ uint4 *slope(int l, int g) const {
     return reinterpret_cast<uint4 *>(slab + (((size_t)l * (kW / 8) + g) * kM + r) * 16);
@@ -454,11 +458,21 @@ struct Epi {
 
 constexpr int kNShort = kW - 3;
 
+// Save mode: columns c0..c0+31 of this row of layer `slot` of a saved array.
+__device__ __forceinline__ void save_chunk(const Epi &e, uint16_t *base, int slot, int c0,
+                                           const uint32_t (&w)[16]) {
+  uint4 *dst = reinterpret_cast<uint4 *>(base + (((size_t)slot * e.n_pad + e.row) * kW + c0));
+#pragma unroll
+  for (int t = 0; t < 4; ++t) dst[t] = make_uint4(w[4 * t], w[4 * t + 1], w[4 * t + 2], w[4 * t + 3]);
+}
+
 // One 32-column chunk of a forward epilogue (layers 1 .. L-1).
 // The 16 packed words of the next A operand go to `hw`; the caller stores them.
-template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP>
+// In save mode the last layer's activations h_{L-1} (its A words hold
+// delta_{L-1}) go to `hx`.
+template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP, bool kSave = false>
 __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uint32_t (&raw)[32],
-                                          Acc &acc, uint32_t (&hw)[16]) {
+                                          Acc &acc, uint32_t (&hw)[16], uint32_t (&hx)[16]) {
   const int b = l * kW + c0;     // bias index
   uint32_t sw[16];
   if constexpr (!LAST && !FEEDS_SKIP) {
@@ -521,6 +535,10 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
       if (LAST) {
         const float wo = comp(wq, u);
         acc.f = fmaf(wo, hv[u], acc.f);
+        if constexpr (kSave) {
+          if (u & 1) hx[2 * q + (u >> 1)] = Op<kF16>::pack(__uint_as_float(hx[2 * q + (u >> 1)]), hv[u]);
+          else hx[2 * q + (u >> 1)] = __float_as_uint(hv[u]);
+        }
         hv[u] = sv[u] * wo;                        // delta_{L-1}
         if (AT_SKIP) {                             // delta_s feeds the direct term
           acc.gx = fmaf(hv[u], comp(s0, u) * kInvSqrt2, acc.gx);
@@ -548,30 +566,43 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
 // A forward epilogue over the thread's 128 columns of column half h, TMEM
 // loads double-buffered; after the first two chunks it arrives on `mid`
 // (when non-zero).
-template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP>
+template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP, bool kSave>
 __device__ __forceinline__ void fwd_half(const Epi &e, int l, int h, Acc &acc, Gate &gate,
                                          uint32_t mid) {
   uint32_t ra[32], rb[32];
   const int cbase = 256 * h + 128 * e.ch;
   tmem_ld32_async(e.t_row + cbase, ra);
 #pragma unroll 1
+  // save mode: h_l (or, in the last layer, delta_{L-1} and h_{L-1})
+  auto save = [&](int c0, const uint32_t (&hw)[16], const uint32_t (&hx)[16]) {
+    if constexpr (kSave) {
+      if (LAST) {
+        save_chunk(e, e.save_d, l, c0, hw);
+        save_chunk(e, e.save_h, l, c0, hx);
+      } else {
+        save_chunk(e, e.save_h, l, c0, hw);
+      }
+    }
+  };
   for (int cc = 0; cc < 4; cc += 2) {
-    uint32_t hw[16];
+    uint32_t hw[16], hx[16];
     tmem_wait_ld(ra);
     tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
-    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * cc, ra, acc, hw);
+    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP, kSave>(e, l, cbase + 32 * cc, ra, acc, hw, hx);
     gate.pass(cc >> 1);
     store_a_chunk(e.A, e.r, cbase + 32 * cc, hw);
+    save(cbase + 32 * cc, hw, hx);
     tmem_wait_ld(rb);
     if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
-    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP>(e, l, cbase + 32 * (cc + 1), rb, acc, hw);
+    fwd_chunk<kF16, LAST, AT_SKIP, FEEDS_SKIP, kSave>(e, l, cbase + 32 * (cc + 1), rb, acc, hw, hx);
     store_a_chunk(e.A, e.r, cbase + 32 * (cc + 1), hw);
+    save(cbase + 32 * (cc + 1), hw, hx);
     if (cc == 0 && mid != 0u) epi_arrive(mid, e.lane);
   }
 }
 
 // L0 (K = 3) on CUDA cores: no TMEM, same epilogue.
-template <bool kF16, bool FEEDS_SKIP>
+template <bool kF16, bool FEEDS_SKIP, bool kSave>
 __device__ __forceinline__ void layer0(const Epi &e) {
 #pragma unroll 1
   for (int cc = 0; cc < 8; ++cc) {
@@ -599,6 +630,7 @@ __device__ __forceinline__ void layer0(const Epi &e) {
       sw[2 * q + 1] = Op<true>::pack(sv[2], sv[3]);
     }
     store_a_chunk(e.A, e.r, c0, hw);
+    if constexpr (kSave) save_chunk(e, e.save_h, 0, c0, hw);
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       st_slope(e.slope(0, (c0 >> 3) + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
@@ -671,7 +703,7 @@ __device__ __forceinline__ void discard_chunk(const Epi &e, int l, int c0) {
 // loads and the slopes of the next chunk are fetched while the current chunk
 // is processed; after the first two chunks it arrives on `mid` (when
 // non-zero).
-template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT>
+template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT, bool kSave>
 __device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, Gate &gate,
                                          uint32_t mid) {
   uint32_t ra[32], rb[32];
@@ -693,6 +725,7 @@ __device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, G
       gate.pass(cc >> 1);
       store_a_chunk(e.A, e.r, cbase + 32 * cc, dw);
     }
+    if constexpr (kSave) save_chunk(e, e.save_d, l - 1, cbase + 32 * cc, dw);   // delta_{l-1}
     discard_chunk(e, l - 1, cbase + 32 * cc);
     if (cc + 2 < 4) {
 #pragma unroll
@@ -702,12 +735,15 @@ __device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, G
     if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
     bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * (cc + 1), rb, sb, acc, dw);
     if (!TO_INPUT) store_a_chunk(e.A, e.r, cbase + 32 * (cc + 1), dw);
+    if constexpr (kSave) save_chunk(e, e.save_d, l - 1, cbase + 32 * (cc + 1), dw);
     discard_chunk(e, l - 1, cbase + 32 * (cc + 1));
     if (cc == 0 && mid != 0u) epi_arrive(mid, e.lane);
   }
 }
 
-template <bool kF16>
+// kSave: the training form, which also writes every layer's A operand out
+// (QueryParams::save_h / save_d) for the weight-gradient products.
+template <bool kF16, bool kSave = false>
 __global__ void __launch_bounds__(kThreads, 1)
     query_tc16_kernel(const QueryParams prm, const __grid_constant__ CUtensorMap tmap_fwd,
                       const __grid_constant__ CUtensorMap tmap_bwd) {
@@ -933,6 +969,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     e.neg_bl2e = -prm.beta * 1.4426950408889634f;
     e.inv_beta = 1.0f / prm.beta;
     e.gbias = prm.bias;
+    e.save_h = prm.save_h;
+    e.save_d = prm.save_d;
+    e.n_pad = ntiles * kM;
     e.pol = l2_evict_first_policy();
     e.kh.neg_bl2e = __float2half2_rn(-prm.beta * 1.4426950408889634f);
     e.kh.inv_beta = __float2half2_rn(1.0f / prm.beta);
@@ -953,6 +992,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t it = 0; ok && it < iters; ++it) {
       const int64_t tile = blockIdx.x + it * gridDim.x;
       const int64_t idx = tile * kM + r;
+      e.row = idx;
       float4 pw = make_float4(0.f, 0.f, 0.f, 0.f);
       if (idx < prm.n) pw = prm.pts[idx];
       e.px = pw.x; e.py = pw.y; e.pz = pw.z;
@@ -965,8 +1005,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       Acc acc;
 
       // ---- L0 on CUDA cores ----
-      if (skip == 1) layer0<kF16, true>(e);
-      else layer0<kF16, false>(e);
+      if (skip == 1) layer0<kF16, true, kSave>(e);
+      else layer0<kF16, false, kSave>(e);
       arrive(a_lo);
       arrive(a_hi_a);
       arrive(a_hi_b);
@@ -980,14 +1020,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!begin_half(h, gate)) { fail(); ok = false; break; }
           const uint32_t mid = h == 1 ? a_hi_a : 0u;
           if (last) {
-            if (at) fwd_half<kF16, true, true, false>(e, l, h, acc, gate, mid);
-            else fwd_half<kF16, true, false, false>(e, l, h, acc, gate, mid);
+            if (at) fwd_half<kF16, true, true, false, kSave>(e, l, h, acc, gate, mid);
+            else fwd_half<kF16, true, false, false, kSave>(e, l, h, acc, gate, mid);
           } else if (at) {
-            fwd_half<kF16, false, true, false>(e, l, h, acc, gate, mid);
+            fwd_half<kF16, false, true, false, kSave>(e, l, h, acc, gate, mid);
           } else if (feeds) {
-            fwd_half<kF16, false, false, true>(e, l, h, acc, gate, mid);
+            fwd_half<kF16, false, false, true, kSave>(e, l, h, acc, gate, mid);
           } else {
-            fwd_half<kF16, false, false, false>(e, l, h, acc, gate, mid);
+            fwd_half<kF16, false, false, false, kSave>(e, l, h, acc, gate, mid);
           }
           gate.pass_all();
           if (!gate.ok) { fail(); ok = false; break; }
@@ -1007,14 +1047,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!begin_half(h, gate)) { fail(); ok = false; break; }
           const uint32_t mid = h == 1 ? a_hi_a : 0u;
           if (to_input) {
-            if (at) bwd_half<kF16, true, false, true>(e, l, h, acc, gate, 0u);
-            else bwd_half<kF16, false, false, true>(e, l, h, acc, gate, 0u);
+            if (at) bwd_half<kF16, true, false, true, kSave>(e, l, h, acc, gate, 0u);
+            else bwd_half<kF16, false, false, true, kSave>(e, l, h, acc, gate, 0u);
           } else if (at) {
-            bwd_half<kF16, true, false, false>(e, l, h, acc, gate, mid);
+            bwd_half<kF16, true, false, false, kSave>(e, l, h, acc, gate, mid);
           } else if (makes) {
-            bwd_half<kF16, false, true, false>(e, l, h, acc, gate, mid);
+            bwd_half<kF16, false, true, false, kSave>(e, l, h, acc, gate, mid);
           } else {
-            bwd_half<kF16, false, false, false>(e, l, h, acc, gate, mid);
+            bwd_half<kF16, false, false, false, kSave>(e, l, h, acc, gate, mid);
           }
           gate.pass_all();
           if (!gate.ok) { fail(); ok = false; break; }
@@ -1162,15 +1202,15 @@ size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid) {
   return (size_t)grid * (size_t)(n_hidden - 1) * kW * kM * 2;   // 16-bit slopes
 }
 
-template <bool kF16>
+template <bool kF16, bool kSave>
 cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cudaStream_t s) {
   // the register split inside the kernel is only valid for this count
   cudaFuncAttributes fa{};
-  cudaError_t e = cudaFuncGetAttributes(&fa, query_tc16_kernel<kF16>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, query_tc16_kernel<kF16, kSave>);
   if (e != cudaSuccess) return e;
   if (fa.numRegs != kLaunchRegs) return cudaErrorInvalidConfiguration;
-  e = cudaFuncSetAttribute(query_tc16_kernel<kF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kSmemBytes);
+  e = cudaFuncSetAttribute(query_tc16_kernel<kF16, kSave>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   const int grid = query_tc16_grid(p.width, p.n, num_sms);
   cudaLaunchConfig_t cfg = {};
@@ -1185,14 +1225,16 @@ cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cu
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, query_tc16_kernel<kF16>, p, net.tmap_fwd, net.tmap_bwd);
+  e = cudaLaunchKernelEx(&cfg, query_tc16_kernel<kF16, kSave>, p, net.tmap_fwd, net.tmap_bwd);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bool fp16,
                                   int num_sms, cudaStream_t s) {
-  return fp16 ? launch_t<true>(p, net, num_sms, s) : launch_t<false>(p, net, num_sms, s);
+  if (p.save_h)
+    return fp16 ? launch_t<true, true>(p, net, num_sms, s) : launch_t<false, true>(p, net, num_sms, s);
+  return fp16 ? launch_t<true, false>(p, net, num_sms, s) : launch_t<false, false>(p, net, num_sms, s);
 }
 
 }  // namespace nsdf
