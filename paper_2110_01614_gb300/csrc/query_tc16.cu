@@ -459,8 +459,11 @@ struct Epi {
 constexpr int kNShort = kW - 3;
 
 // Save mode: columns c0..c0+31 of this row of layer `slot` of a saved array.
+// Rows past n_pad belong to the fully masked tiles that every CTA walks so
+// that the cluster's CTAs stay in step; they are not saved.
 __device__ __forceinline__ void save_chunk(const Epi &e, uint16_t *base, int slot, int c0,
                                            const uint32_t (&w)[16]) {
+  if (e.row >= e.n_pad) return;
   uint4 *dst = reinterpret_cast<uint4 *>(base + (((size_t)slot * e.n_pad + e.row) * kW + c0));
 #pragma unroll
   for (int t = 0; t < 4; ++t) dst[t] = make_uint4(w[4 * t], w[4 * t + 1], w[4 * t + 2], w[4 * t + 3]);

@@ -17,7 +17,11 @@
   the paper's Table 1 quotes 255 ms / 350 ms for 1M queries on a Tesla T4
   (context only: other hardware, other weights).
 
-Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped cloth paper_arch]
+* fit512: the 512-wide body-scale network fitted with the paper's L1 loss on
+  the BF16 tensor-core path (pool of 1,048,576 points with exact targets,
+  batches of 250,000): seconds per step and the time of nsdf_l1_grad alone.
+
+Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped cloth paper_arch fit512]
 """
 
 import json
@@ -143,13 +147,33 @@ def bench_paper_arch(reps=10):
     return res
 
 
+def bench_fit512(steps=20):
+    from . import nsdf_l1_grad
+    from .fit import MeshFitTC
+    V, F = synth.displaced_icosphere(level=5, seed=7)
+    fit = MeshFitTC(BODY, V, F, precision=NSDF_BF16, pool_points=1 << 20, batch=250_000)
+    fit.run(2)
+    losses, s_per_step = fit.run(steps)
+    P, d = fit.pool_P[:250_000], fit.pool_d[:250_000]
+    ms = events_ms(lambda: nsdf_l1_grad(fit.net.ctx, P, d, fit.grad, fit.loss), 5)
+    fit.close()
+    # algorithmic work of the gradient: the query's forward and J^T products
+    # (3,670,528 MAC per point) plus the weight-gradient products
+    # (7 x 512 x 512 MAC per point)
+    mac = 3_670_528 + 7 * 512 * 512
+    return {"workload": "fit512", "precision": "bf16", "batch": 250_000, "pool": 1 << 20,
+            "s_per_step": s_per_step, "l1_grad_ms": ms,
+            "l1_grad_tflops": 2 * mac * 250_000 / (ms * 1e-3) / 1e12,
+            "loss_first": losses[0], "loss_last": losses[-1]}
+
+
 def main(argv):
-    which = argv or ["fit", "penalty", "grouped", "cloth", "paper_arch"]
+    which = argv or ["fit", "penalty", "grouped", "cloth", "paper_arch", "fit512"]
     torch.cuda.set_device(0)
     for w in which:
         t0 = time.perf_counter()
         r = {"fit": bench_fit, "penalty": bench_penalty, "grouped": bench_grouped,
-             "cloth": bench_cloth, "paper_arch": bench_paper_arch}[w]()
+             "cloth": bench_cloth, "paper_arch": bench_paper_arch, "fit512": bench_fit512}[w]()
         r["wall_s"] = time.perf_counter() - t0
         print(json.dumps(r), flush=True)
 

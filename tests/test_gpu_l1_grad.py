@@ -33,18 +33,27 @@ def nsdf(nsdf_lib):
     return m
 
 
-@pytest.fixture(scope="module")
-def problem():
-    n = 1000                                   # several tiles and a ragged tail
+def make_problem(n, seed):
     blob = synth.geometric_init(BODY, 0)
-    pts = synth.body_scale_points(n, 17)
+    pts = synth.body_scale_points(n, seed)
     f, _, _ = mlp.forward(blob, BODY, pts[:, :3])
-    s = synth.Stream(18)
+    s = synth.Stream(seed + 1)
     off = s.uniform(n, 0.01, 0.1) * np.where(s.uniform(n) < 0.5, -1.0, 1.0)
     d = (f + off).astype(np.float32)
     a = np.sign(f - d.astype(np.float64)) / n
     g_ref, _ = mlp.loss_backward(blob, BODY, pts[:, :3], a, np.zeros((n, 3)))
     return blob, pts, d, g_ref, np.abs(f - d).mean()
+
+
+@pytest.fixture(scope="module")
+def problem():
+    return make_problem(1000, 17)              # several tiles and a ragged tail
+
+
+@pytest.fixture(scope="module")
+def big_problem():
+    # more tiles than CTAs: every CTA also walks fully masked tiles
+    return make_problem(25_000, 21)
 
 
 def blocks(arch):
@@ -58,8 +67,7 @@ def blocks(arch):
     return out
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_l1_grad_matches_oracle_and_is_deterministic(nsdf, problem, prec):
+def check_l1_grad(nsdf, problem, prec):
     blob, pts, d, g_ref, loss_ref = problem
     p = nsdf.NSDF_BF16 if prec == "bf16" else nsdf.NSDF_FP16
     net = nsdf.NeuralSDF(BODY, p).load(blob)
@@ -87,7 +95,16 @@ def test_l1_grad_matches_oracle_and_is_deterministic(nsdf, problem, prec):
         err = np.linalg.norm(g1[sl] - ref) / nrm
         worst = max(worst, err)
         assert err <= TOL[prec], (name, err)
-    print(prec, "worst relative layer error", worst)
+    print(prec, len(pts), "points: worst relative layer error", worst)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_l1_grad_matches_oracle_and_is_deterministic(nsdf, problem, prec):
+    check_l1_grad(nsdf, problem, prec)
+
+
+def test_l1_grad_with_more_tiles_than_ctas(nsdf, big_problem):
+    check_l1_grad(nsdf, big_problem, "bf16")
 
 
 def test_l1_grad_rejects_fp32_contexts_and_empty_batches(nsdf, problem):
