@@ -46,8 +46,8 @@ FLOP_PER_QUERY = 2 * MAC_PER_QUERY
 # SHA-256 of the kernel source it was taken on; reported only while the
 # source is unchanged.
 TRAFFIC_CAPTURE = {
-    "source_sha256": "7203aac45c55c8ef1fe12c76bbfd783aa0e9b6aaf255dab89bf21f8513d417bf",
-    "bytes_per_launch": 3.862205e9 + 4.801872e9,
+    "source_sha256": "e52be038019ef2319bed3e1ef928cfdb1e4f40cc03ae5a352e2f1e69236cbb8f",
+    "bytes_per_launch": 4.004132e9 + 4.874528e9,
 }
 
 
