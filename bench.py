@@ -142,14 +142,21 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def max_over_ranks(x, world, device="cuda"):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(world, n, steps, local_seconds, device="cuda"):
+    """Whole-job queries/s of a weak-scaling run: every rank's n points per
+    step over the slowest rank's time; returns (queries/s, that time)."""
+    t = max_over_ranks(local_seconds, world, device)
+    return world * n * steps / t, t
 
 
 def oracle_rate(pts, blob, budget_s):
@@ -276,8 +283,7 @@ def run_gpu(args):
     clocks.start()
     durs = timed_steps(bf, args.steps, max(args.warmup, 3))
     clk = clocks.stop()
-    t_total = max_over_ranks(sum(durs), world)
-    value = world * n * args.steps / t_total
+    value, t_total = job_throughput(world, n, args.steps, sum(durs))
     kernel_s = statistics.mean(durs)
     sample_idx = np.sort(synth.Stream(99).u64(min(4096, n)) % np.uint64(n)).astype(np.int64)
     bf_ns, bf_hit = out_ns.cpu().numpy(), out_hit.cpu().numpy().astype(bool)
@@ -309,8 +315,7 @@ def run_gpu(args):
             t0 = time.perf_counter()
             nsdf.nsdf_collide(bf.ctx, h_pts, EPS, h_out, h_ns, h_hit)   # results on host on return
             e2e_t.append(time.perf_counter() - t0)
-        e2e_total = max_over_ranks(sum(e2e_t), world)
-        e2e_value = world * n * args.steps / e2e_total
+        e2e_value, _ = job_throughput(world, n, args.steps, sum(e2e_t))
 
     peak_tf, hbm, peak_kind = load_peaks()
     achieved_tf = FLOP_PER_QUERY * n / kernel_s / 1e12
