@@ -7,12 +7,14 @@
 //   * each hidden layer z_l = W_l x_l (Eq. 1) as 64 tcgen05.mma
 //     (M=128, N=256, K=16; 16-bit x 16-bit -> FP32) into TMEM, A = the
 //     activation tile resident in shared memory (128 x 512, 128-byte
-//     swizzled K-major), B = weight panels streamed by TMA through a
-//     3-stage ring,
-//   * the epilogue warps read z from TMEM (tcgen05.ld), add the bias and
-//     write softplus_beta(z) back as the next A operand, and park
+//     swizzled K-major), B = 256 x 64 weight panels streamed by TMA
+//     through a 2-stage ring, each panel fetched half by each CTA of a
+//     2-CTA cluster and multicast into both,
+//   * the epilogue warps read z from TMEM (tcgen05.ld), add the bias (the
+//     biases, W_0, the skip weights on p and w_out sit in shared memory)
+//     and write softplus_beta(z) back as the next A operand, and park
 //     sigmoid(beta z) (the slope the reverse chain needs) in a per-CTA
-//     scratch slab (16-bit, lane-contiguous, L2-resident),
+//     scratch slab (FP16, lane-contiguous, stored evict-first in L2),
 //   * the skip connection's input columns p/sqrt(2) never pass through the
 //     16-bit operands: their product with W_s is added in FP32 on CUDA
 //     cores, and their gradient is accumulated in FP32 from delta_s,
@@ -23,6 +25,8 @@
 //     connection's 1/sqrt(2) split, and grad f = W_0^T delta_0 in FP32,
 //   * Eq. 2, the test f < eps and the contact point of Eq. 3 (with the
 //     rigid transform of Sec. 4.2) in the final epilogue; float4 stores.
+// A training form of the same kernel (kSave) also writes every A operand out
+// for the weight-gradient products of the fitting loss (train.cu).
 //
 // Warp roles (384 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
 // TMEM owner, warps 2, 3 idle, warps 4..11 = epilogue (warp w reads TMEM
