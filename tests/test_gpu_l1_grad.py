@@ -121,3 +121,33 @@ def test_l1_grad_rejects_fp32_contexts_and_empty_batches(nsdf, problem):
         nsdf.nsdf_l1_grad(net.ctx, P[:0], D[:0], g)
     assert e.value.status == 1
     net.close()
+
+
+@pytest.mark.parametrize("arch", [synth.Arch(3, 512, 2, -1, 100.0), synth.Arch(3, 512, 5, 1, 100.0),
+                                  synth.Arch(3, 512, 4, 3, 100.0)],
+                         ids=["2-layers-no-skip", "5-layers-skip-at-1", "4-layers-skip-at-3"])
+def test_l1_grad_other_shapes(nsdf, arch):
+    """Other depths and skip positions: the skip layer's p columns, a skip at
+    L1 (L0 then feeds it) and no skip at all go through other branches of the
+    gradient's assembly."""
+    n = 700
+    blob = synth.geometric_init(arch, 3)
+    pts = synth.body_scale_points(n, 31)
+    f, _, _ = mlp.forward(blob, arch, pts[:, :3])
+    s = synth.Stream(32)
+    d = (f + s.uniform(n, 0.01, 0.1) * np.where(s.uniform(n) < 0.5, -1.0, 1.0)).astype(np.float32)
+    g_ref, _ = mlp.loss_backward(blob, arch, pts[:, :3], np.sign(f - d.astype(np.float64)) / n,
+                                 np.zeros((n, 3)))
+    net = nsdf.NeuralSDF(arch, nsdf.NSDF_BF16).load(blob)
+    g = torch.full((blob.size,), float("nan"), device="cuda")
+    nsdf.nsdf_l1_grad(net.ctx, torch.from_numpy(pts).cuda(), torch.from_numpy(d).cuda(), g)
+    nsdf.nsdf_sync_status(net.ctx)
+    net.close()
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.isfinite(g).all()
+    for name, sl in blocks(arch):
+        nrm = np.linalg.norm(g_ref[sl])
+        if nrm == 0.0:
+            assert np.abs(g[sl]).max() <= 1e-6, name
+            continue
+        assert np.linalg.norm(g[sl] - g_ref[sl]) / nrm <= TOL["bf16"], name
