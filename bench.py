@@ -44,11 +44,10 @@ FLOP_PER_QUERY = 2 * MAC_PER_QUERY
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the tensor-core kernel on this workload, from one ncu capture, keyed by the
 # SHA-256 of the kernel source's code (comments and blank lines removed) it was
-# taken on; reported only while that code is unchanged.  The capture's full
-# file hash was e52be038019ef2319bed3e1ef928cfdb1e4f40cc03ae5a352e2f1e69236cbb8f.
+# taken on; reported only while that code is unchanged.
 TRAFFIC_CAPTURE = {
-    "code_sha256": "166d88f5b6e2bb7b6425eab88f1ec77e1ce4987f999a5d00476f47e06855a294",
-    "bytes_per_launch": 4.004132e9 + 4.874528e9,
+    "code_sha256": "6f239a4a737f9a6ec9acc3bca1e8fc8e41b2d4bc646091ec4aa5d97d4701c722",
+    "bytes_per_launch": 3.939950e9 + 4.830467e9,
 }
 
 
