@@ -71,15 +71,25 @@ __global__ void l1_loss_kernel(const float *__restrict__ loss_part, int nb, int6
   *loss = (float)(t / (double)n);
 }
 
-// delta rows times a_i: flip the sign bit of both halves of a word, or zero it.
-__global__ void scale_rows_kernel(uint32_t *__restrict__ d, int64_t words, int64_t n_pad, int W,
+// delta rows times a_i: flip the sign bit of every 16-bit value, or zero it
+// (16 bytes = 8 values per access).
+__global__ void scale_rows_kernel(uint4 *__restrict__ d, int64_t vecs, int64_t n_pad, int W,
                                   const float *__restrict__ a) {
-  const int64_t per_row = W / 2;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < words;
+  const int64_t per_row = W / 8;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < vecs;
        t += (int64_t)gridDim.x * blockDim.x) {
     const float s = a[(t / per_row) % n_pad];
-    const uint32_t v = d[t];
-    d[t] = s == 0.f ? 0u : (s < 0.f ? v ^ 0x80008000u : v);
+    if (s > 0.f) continue;
+    uint4 v = d[t];
+    if (s == 0.f) {
+      v = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      v.x ^= 0x80008000u;
+      v.y ^= 0x80008000u;
+      v.z ^= 0x80008000u;
+      v.w ^= 0x80008000u;
+    }
+    d[t] = v;
   }
 }
 
@@ -93,14 +103,14 @@ __device__ __forceinline__ float2 unpack16(uint32_t w, int fp16) {
 //   j == L : sum_i delta_0(i)[c] p_i[k], k = 0..2         (W_0)
 //   j == L+1: sum_i delta_s(i)[c] p_i[k] / sqrt(2)        (skip layer s, its p columns)
 //   j == L+2: sum_i a_i h_{L-1}(i)[c]; and sum_i a_i      (w_out, b_out)
-// Thread t covers columns 2t, 2t+1; part[j][block][c][3].
+// Thread t covers columns 8t .. 8t+7 (one 16-byte load per row); part[j][block][c][3].
 __global__ void small_partials_kernel(const uint16_t *__restrict__ save_h,
                                       const uint16_t *__restrict__ save_d,
                                       const float4 *__restrict__ pts, const float *__restrict__ a,
                                       int L, int W, int skip, int64_t n, int64_t n_pad, int fp16,
                                       float *__restrict__ part) {
   const int j = blockIdx.y;
-  const int c = 2 * threadIdx.x;
+  const int c = 8 * threadIdx.x;
   if (c >= W) return;
   const int64_t r0 = (int64_t)blockIdx.x * kRowsPerBlock;
   int64_t r1 = r0 + kRowsPerBlock;
@@ -110,38 +120,46 @@ __global__ void small_partials_kernel(const uint16_t *__restrict__ save_h,
   else if (j == L) src = save_d;
   else if (j == L + 1) src = skip > 0 ? save_d + (size_t)skip * n_pad * W : nullptr;
   else src = save_h + (size_t)(L - 1) * n_pad * W;
-  float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float acc[8][3];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u][0] = acc[u][1] = acc[u][2] = 0.f;
   float asum = 0.f;
   if (src) {
     for (int64_t r = r0; r < r1; ++r) {
-      const float2 v = unpack16(*reinterpret_cast<const uint32_t *>(src + (size_t)r * W + c), fp16);
+      const uint4 w = *reinterpret_cast<const uint4 *>(src + (size_t)r * W + c);
+      const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 f2 = unpack16(ww[u], fp16);
+        v[2 * u] = f2.x;
+        v[2 * u + 1] = f2.y;
+      }
       if (j < L) {
-        acc[0][0] += v.x;
-        acc[1][0] += v.y;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u][0] += v[u];
       } else if (j <= L + 1) {
         float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
         if (r < n) p = pts[r];
         const float sc = j == L ? 1.f : kInvSqrt2;
         const float q[3] = {p.x * sc, p.y * sc, p.z * sc};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          acc[0][k] = fmaf(v.x, q[k], acc[0][k]);
-          acc[1][k] = fmaf(v.y, q[k], acc[1][k]);
-        }
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) acc[u][k] = fmaf(v[u], q[k], acc[u][k]);
       } else {
         const float s = a[r];
-        acc[0][0] = fmaf(s, v.x, acc[0][0]);
-        acc[1][0] = fmaf(s, v.y, acc[1][0]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u][0] = fmaf(s, v[u], acc[u][0]);
         asum += s;
       }
     }
   }
   float *o = part + (((size_t)j * gridDim.x + blockIdx.x) * W + c) * 3;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    o[k] = acc[0][k];
-    o[3 + k] = acc[1][k];
-  }
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[3 * u + k] = acc[u][k];
   if (j == L + 2 && threadIdx.x == 0) o[2] = asum;   // column 0, slot 2: sum a_i
 }
 
@@ -297,9 +315,9 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
   const int lb = (int)((n_pad + 255) / 256);
   l1_sign_kernel<<<lb, 256, 0, s>>>(t->ns, targets, n, n_pad, t->a, t->loss_part);
   l1_loss_kernel<<<1, 32, 0, s>>>(t->loss_part, lb, n, loss ? loss : t->loss_tmp);
-  const int64_t words = (int64_t)L * n_pad * W / 2;
-  scale_rows_kernel<<<8 * num_sms, 256, 0, s>>>(reinterpret_cast<uint32_t *>(t->save_d), words,
-                                                n_pad, W, t->a);
+  const int64_t vecs = (int64_t)L * n_pad * W / 8;
+  scale_rows_kernel<<<8 * num_sms, 256, 0, s>>>(reinterpret_cast<uint4 *>(t->save_d), vecs, n_pad,
+                                                W, t->a);
   // 3. hidden-layer weight gradients: G_l[n][k] = sum_i delta_l(i)[n] h_{l-1}(i)[k]
   if (cublasSetStream(t->blas, s) != CUBLAS_STATUS_SUCCESS) return NSDF_ERR_CUDA;
   const cudaDataType_t dt = fp16 ? CUDA_R_16F : CUDA_R_16BF;
@@ -314,7 +332,7 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
       return NSDF_ERR_CUDA;
   }
   // 4. the small sums, reduced in block order
-  small_partials_kernel<<<dim3(nb, jobs), W / 2, 0, s>>>(t->save_h, t->save_d, p.pts, t->a, L, W,
+  small_partials_kernel<<<dim3(nb, jobs), W / 8, 0, s>>>(t->save_h, t->save_d, p.pts, t->a, L, W,
                                                          p.skip, n, n_pad, fp16 ? 1 : 0, t->part);
   const int64_t nsmall = (int64_t)jobs * W * 3;
   small_reduce_kernel<<<(int)((nsmall + 255) / 256), 256, 0, s>>>(t->part, jobs, nb, W, t->small);
