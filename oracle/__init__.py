@@ -16,6 +16,9 @@ Contents, each function citing the passage of the paper it follows:
 * ``mesh`` - exact signed distance to a watertight triangle mesh by brute
   force (the ground truth a network is fitted to, Sec. 3.1): closest point on
   a triangle, sign from the generalized winding number.
+* ``rounded`` - the Fourier-feature ReLU network of Sec. 4.3 with its
+  tensor-core operands rounded to a 16-bit format, so that the ReLU
+  decisions are taken in the precision of the 16-bit kernels.
 * ``cloth`` - one explicit Verlet step of a mass-spring quad cloth followed
   by the collision solve (Sec. 4.1).
 
@@ -24,4 +27,4 @@ finite differences in ``tests/test_oracle_*.py``; the paper prints no worked
 numerical example, so nothing is pinned to a printed value.
 """
 
-from . import mlp, mesh, cloth  # noqa: F401
+from . import mlp, mesh, cloth, rounded  # noqa: F401

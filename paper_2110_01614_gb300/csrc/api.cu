@@ -118,6 +118,11 @@ __global__ void pack_weights_kernel(const float *__restrict__ blob, PackPlan pla
       const int r = (int)(t / W), c = (int)(t % W);
       net.ff0_t[t] = W0[(int64_t)c * W + r];   // [k=r][n=c] = W_0[n][k]
       net.ff0[t] = W0[t];                      // [n=r][k=c] = W_0[n][k]
+      if (net.fwd16) {
+        // slot 0 of the 16-bit copies, feature columns / rows permuted
+        net.fwd16[t] = to16(W0[(int64_t)r * W + ff_feature_of_column(c, plan.ff)], net.fp16);
+        net.bwd16[t] = to16(W0[(int64_t)c * W + ff_feature_of_column(r, plan.ff)], net.fp16);
+      }
     }
   } else {
     for (int64_t t = t0; t < (int64_t)W * 3; t += stride) {
@@ -145,8 +150,10 @@ __global__ void pack_weights_kernel(const float *__restrict__ blob, PackPlan pla
     net.fwd_t[o] = w_cr;   // [k=r][n=c] = W_l[n][k]
     net.bwd[o] = w_rc;     // [n=r][k=c] = W_l[n][k]
     if (net.fwd16) {
-      net.fwd16[o] = to16(w_rc, net.fp16);   // [n=r][k=c]
-      net.bwd16[o] = to16(w_cr, net.fp16);   // [k=r][n=c]
+      // Fourier-feature nets keep layer 0 in slot 0 of the 16-bit copies
+      const int64_t o16 = plan.ff > 0 ? o + per : o;
+      net.fwd16[o16] = to16(w_rc, net.fp16);   // [n=r][k=c]
+      net.bwd16[o16] = to16(w_cr, net.fp16);   // [k=r][n=c]
     }
   }
 }
@@ -211,12 +218,17 @@ nsdf_status ctx_alloc(nsdf_ctx *ctx, T **p, size_t count) {
 // BF16 and FP16 contexts share the 16-bit tensor-core kernel.
 bool use_bf16(const nsdf_ctx *ctx) { return ctx->prec == NSDF_BF16 || ctx->prec == NSDF_FP16; }
 
+// 16-bit Fourier-feature ReLU contexts run query_tc16_ff.cu.
+bool use_tc16_ff(const nsdf_ctx *ctx) { return use_bf16(ctx) && ctx->arch.ff_freqs > 0; }
+
 int query_grid(const nsdf_ctx *ctx, int64_t n) {
+  if (use_tc16_ff(ctx)) return query_tc16_ff_grid(n, ctx->num_sms);
   if (use_bf16(ctx)) return query_tc16_grid(ctx->arch.width, n, ctx->num_sms);
   return query_fp32_grid(ctx->arch.width, n, ctx->num_sms, ctx->arch.ff_freqs > 0);
 }
 
 size_t query_scratch(const nsdf_ctx *ctx, int grid) {
+  if (use_tc16_ff(ctx)) return 0;
   if (use_bf16(ctx)) return query_tc16_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
   return query_fp32_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
 }
@@ -253,6 +265,8 @@ void fill_net(const nsdf_ctx *ctx, int net, QueryParams &p) {
 }
 
 cudaError_t launch_query(const nsdf_ctx *ctx, int net, const QueryParams &p, cudaStream_t s) {
+  if (use_tc16_ff(ctx))
+    return launch_query_tc16_ff(p, ctx->nets[net], ctx->prec == NSDF_FP16, ctx->num_sms, s);
   if (use_bf16(ctx))
     return launch_query_tc16_net(p, ctx->nets[net], ctx->prec == NSDF_FP16, ctx->num_sms, s);
   return launch_query_fp32(p, ctx->num_sms, s);
@@ -430,10 +444,14 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
   if (!arch_valid(arch) || n_nets < 1 || n_nets > 4096) return NSDF_ERR_INVALID_ARG;
   if (prec != NSDF_FP32 && prec != NSDF_BF16 && prec != NSDF_FP16) return NSDF_ERR_INVALID_ARG;
   if (prec == NSDF_FP32 && !query_fp32_supported(arch->width)) return NSDF_ERR_UNSUPPORTED;
-  if (prec != NSDF_FP32 &&
-      (arch->activation != NSDF_ACT_SOFTPLUS || arch->ff_freqs > 0 ||
-       !query_tc16_supported(arch->width, arch->n_hidden, arch->skip_layer)))
-    return NSDF_ERR_UNSUPPORTED;
+  if (prec != NSDF_FP32) {
+    const bool ff_relu = arch->ff_freqs > 0 &&
+                         query_tc16_ff_supported(arch->width, arch->n_hidden, arch->ff_freqs,
+                                                 arch->activation == NSDF_ACT_RELU);
+    const bool softplus = arch->ff_freqs == 0 && arch->activation == NSDF_ACT_SOFTPLUS &&
+                          query_tc16_supported(arch->width, arch->n_hidden, arch->skip_layer);
+    if (!ff_relu && !softplus) return NSDF_ERR_UNSUPPORTED;
+  }
   nsdf_ctx *ctx = new (std::nothrow) nsdf_ctx;
   if (!ctx) return NSDF_ERR_OOM;
   ctx->arch = *arch;
@@ -463,8 +481,9 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
       if (st == NSDF_OK) st = ctx_alloc(ctx, &d.ff0, (size_t)W * W);
     }
     if (st == NSDF_OK && prec != NSDF_FP32) {
-      st = ctx_alloc(ctx, &d.fwd16, hid);
-      if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd16, hid);
+      const size_t n16 = arch->ff_freqs > 0 ? (size_t)L * W * W : hid;   // + layer 0
+      st = ctx_alloc(ctx, &d.fwd16, n16);
+      if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd16, n16);
     }
   }
   if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_err, 4);
@@ -551,7 +570,9 @@ nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w, size_t n_f
     if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) return map_err(e);
-  if (use_bf16(ctx) && !make_tc16_tmaps(ctx->nets[net], a.width, a.n_hidden, ctx->prec == NSDF_FP16))
+  const bool fp16 = ctx->prec == NSDF_FP16;
+  if (use_tc16_ff(ctx) ? !make_tc16_ff_tmaps(ctx->nets[net], a.n_hidden, fp16)
+                       : use_bf16(ctx) && !make_tc16_tmaps(ctx->nets[net], a.width, a.n_hidden, fp16))
     return NSDF_ERR_CUDA;
   ctx->nets[net].loaded = true;
   return NSDF_OK;

@@ -77,6 +77,18 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   if (st != NSDF_OK) return st;
   st = ctx_set_transform(T, &p);
   if (st != NSDF_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  p.pts = reinterpret_cast<const float4 *>(pts);
+  p.n = n;
+  p.collide = 1;
+  p.eps = eps;
+  p.out_pts = reinterpret_cast<float4 *>(out_pts);
+  p.out_n_sdf = reinterpret_cast<float4 *>(out_n_sdf);
+  p.out_hit = out_hit;
+  if (tc16 && p.ff > 0) {   // the Fourier-feature tensor-core kernel needs no scratch
+    const cudaError_t e = launch_query_tc16_ff(p, *net, fp16, num_sms, s);
+    return e == cudaSuccess ? NSDF_OK : NSDF_ERR_CUDA;
+  }
   // one slab per CTA; as many CTAs as whole slabs fit.  The launchers size
   // their grid as min(tiles, sm_arg * CTAs per SM), so sm_arg is chosen to
   // keep that product within the slabs the array holds.
@@ -91,15 +103,7 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   const int ctas = (int)sm_arg;
   void *scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return NSDF_ERR_CUDA;
-  p.pts = reinterpret_cast<const float4 *>(pts);
-  p.n = n;
-  p.collide = 1;
-  p.eps = eps;
-  p.out_pts = reinterpret_cast<float4 *>(out_pts);
-  p.out_n_sdf = reinterpret_cast<float4 *>(out_n_sdf);
-  p.out_hit = out_hit;
   p.scratch = static_cast<float *>(scratch);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const cudaError_t e = tc16 ? launch_query_tc16_net(p, *net, fp16, ctas, s)
                              : launch_query_fp32(p, ctas, s);
   return e == cudaSuccess ? NSDF_OK : NSDF_ERR_CUDA;

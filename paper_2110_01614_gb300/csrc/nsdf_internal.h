@@ -36,7 +36,8 @@ struct NetDevice {
   float *ffB = nullptr;    // [m][3]
   float *ff0_t = nullptr;  // [width(k)][width(n)] = W_0[n][k]
   float *ff0 = nullptr;    // [width(n)][width(k)] = W_0[n][k]
-  // 16-bit forms (tensor-core B operands, K-major; BF16 or FP16 bits)
+  // 16-bit forms (tensor-core B operands, K-major; BF16 or FP16 bits);
+  // Fourier-feature networks hold n_hidden layers here, layer 0 first
   uint16_t *fwd16 = nullptr;  // [n_hidden-1][width(n)][width(k)] = W_l
   uint16_t *bwd16 = nullptr;  // [n_hidden-1][width(k)][width(n)] = W_l^T
   // TMA descriptors of fwd16 / bwd16 (16-bit contexts only)
@@ -119,6 +120,21 @@ cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bo
 size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid);
 int query_tc16_grid(int width, int64_t n, int num_sms);
 int query_tc16_min_grid();   // CTAs of one cluster: the smallest grid of the kernel
+
+// 16-bit tensor-core form of the Fourier-feature ReLU networks of Sec. 4.3
+// (width 256, m = 128, 1..8 layers; query_tc16_ff.cu).  Its 16-bit weight
+// copies hold all n_hidden layers, layer l at [l][256][256], layer 0 with the
+// feature columns permuted (ff_feature_of_column).  It needs no scratch.
+bool query_tc16_ff_supported(int width, int n_hidden, int ff, int relu);
+bool make_tc16_ff_tmaps(NetDevice &net, int n_hidden, bool fp16);
+int query_tc16_ff_grid(int64_t n, int num_sms);
+cudaError_t launch_query_tc16_ff(const QueryParams &p, const NetDevice &net, bool fp16,
+                                 int num_sms, cudaStream_t s);
+// Column c = 128 g + 64 s + i of that kernel's feature tile holds feature
+// s * m + 64 g + i of gamma(p) (sines are features 0..m-1, cosines m..2m-1).
+__host__ __device__ inline int ff_feature_of_column(int c, int m) {
+  return ((c >> 6) & 1) * m + 64 * (c >> 7) + (c & 63);
+}
 
 // Context accessors for entry points defined outside api.cu: the network-0
 // launch parameters of a loaded context, and the transform of nsdf_collide.

@@ -1,0 +1,628 @@
+// 16-bit tensor-core form of the fused collision query for the paper's own
+// networks (Sec. 4.3): a Fourier-feature input layer gamma(p) =
+// [sin(2 pi B p), cos(2 pi B p)] of m = 128 frequencies, then ReLU layers of
+// width 256 and one output unit.  BF16 or FP16 operands (one template), FP32
+// accumulation in TMEM.
+//
+// One persistent CTA per SM walks tiles of 128 points.  Per tile the whole
+// query of Sec. 3.2 runs on chip:
+//   * the epilogue warps evaluate gamma(p) on CUDA cores (compensated phase,
+//     sinpi / cospi; see ff_phase.cuh) and write it as the first A operand,
+//   * every layer z_l = W_l x_l (Eq. 1; layer 0 reads gamma(p)) is 16
+//     tcgen05.mma (M=128, N=256, K=16; 16-bit x 16-bit -> FP32) into TMEM,
+//     A = the 128 x 256 activation tile in shared memory (128-byte swizzled
+//     K-major), B = 256 x 64 weight panels streamed by TMA through a 3-stage
+//     ring, each panel fetched half by each CTA of a 2-CTA cluster and
+//     multicast into both,
+//   * the epilogue warps read z from TMEM (tcgen05.ld), add the bias, write
+//     max(z, 0) back over A and keep the ReLU's slope, [z > 0], as one bit
+//     per unit in shared memory (4 KB per layer): the reverse chain needs no
+//     scratch in global memory,
+//   * the last hidden layer's epilogue forms f = w_out . h in FP32 and starts
+//     the reverse chain with delta = [z > 0] * w_out,
+//   * the Jacobian-transpose chain of Sec. 3.2, g_{l-1} = W_l^T delta_l, runs
+//     as the same products against the transposed weights, with
+//     delta_{l-1} = [z_{l-1} > 0] * g_{l-1},
+//   * layer 0's input gradient g_gamma goes through the feature Jacobian in
+//     FP32: grad f = 2 pi sum_j (g_sin,j cos(2 pi b_j.p) - g_cos,j sin(2 pi b_j.p)) b_j,
+//   * Eq. 2, the test f < eps and the contact point of Eq. 3 (with the rigid
+//     transform of Sec. 4.2) in the final epilogue; float4 stores.
+// Within a tile each product and its epilogue run back to back (a product
+// needs the whole previous epilogue); the weight ring fetches the next
+// product's panels while the epilogue runs.
+//
+// The feature tile uses a permuted column order so that each epilogue thread
+// evaluates each of its phases once and uses both its sine and its cosine:
+// column c = 128 g + 64 s + i holds the sine (s = 0) or cosine (s = 1) of
+// frequency j = 64 g + i (ff_feature_of_column); layer 0's weights are packed
+// with their columns in that order, and its transposed copy with its rows.
+//
+// Warp roles (384 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
+// TMEM owner, warps 2, 3 idle, warps 4..11 = epilogue (warp w reads TMEM
+// lanes 32*(w%4)..+31; warps 4..7 take columns 0..127 of every product,
+// warps 8..11 columns 128..255).  Every wait is bounded
+// (QueryParams::wait_budget clock cycles); on expiry the kernel records
+// kDevTimeout, drains what it has in flight and returns.
+
+#include <cudaTypedefs.h>
+
+#include "nsdf_internal.h"
+#include "tc_ptx.cuh"
+#include "ff_phase.cuh"
+
+namespace nsdf {
+namespace {
+
+using namespace ptx;
+
+constexpr int kW = 256;                    // network width handled here
+constexpr int kFreq = kW / 2;              // Fourier frequencies m
+constexpr int kM = 128;                    // points per tile (MMA M, TMEM lanes)
+constexpr int kN = 256;                    // MMA N: a whole layer
+constexpr int kKAtom = 64;                 // K elements per 128-byte swizzle atom
+constexpr int kAtoms = kW / kKAtom;        // 4 weight panels per product
+constexpr int kStages = 3;
+constexpr int kMaxHidden = 8;
+constexpr int kCluster = 2;
+constexpr int kSliceRows = kN / kCluster;
+constexpr int kStageBytes = kN * kKAtom * 2;     // 32 KB weight panel
+constexpr int kABytes = kM * kW * 2;             // 64 KB activation tile
+constexpr int kAtomBytes = kM * kKAtom * 2;      // 16 KB: one K atom of A
+constexpr int kEpiWarps = 8;
+constexpr int kEpiWarp0 = 4;
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
+constexpr float kTwoPi = 6.28318530717958648f;
+
+// shared-memory map (bytes from a 1024-aligned base)
+constexpr int kOffA = 0;
+constexpr int kOffB = kOffA + kABytes;
+constexpr int kOffMask = kOffB + kStages * kStageBytes;          // uint4 [kMaxHidden-1][2][kM]
+constexpr int kOffBias = kOffMask + (kMaxHidden - 1) * 2 * kM * 16;   // float [kMaxHidden][kW]
+constexpr int kOffFreq = kOffBias + kMaxHidden * kW * 4;         // float4 [kFreq]: b_j
+constexpr int kOffWout = kOffFreq + kFreq * 16;                  // float [kW]
+constexpr int kOffExch = kOffWout + kW * 4;                      // float4 [kM]
+constexpr int kOffBar = kOffExch + kM * 16;
+// barriers: full[kStages], empty[kStages], a_ready, d_full, mma_done, x_full, x_empty
+constexpr int kNumBars = 2 * kStages + 5;
+constexpr int kOffTmemSlot = kOffBar + 8 * kNumBars;
+constexpr int kOffAbort = kOffTmemSlot + 4;
+constexpr int kSmemBytes = kOffAbort + 4;
+static_assert(kSmemBytes <= 232448, "shared memory budget");
+static_assert(kAtomBytes == 16384, "store_a_chunk assumes 16 KB atoms");
+
+__device__ __forceinline__ float4 lds4(int off, int idx) {
+  extern __shared__ __align__(1024) uint8_t g_smem_ff[];
+  return reinterpret_cast<const float4 *>(g_smem_ff + off)[idx];
+}
+
+// Tell the MMA issuer (barrier `bar`) that this warp's writes to A, and its
+// reads of TMEM, are done.
+__device__ __forceinline__ void epi_arrive(uint32_t bar, int lane) {
+  fence_proxy_async();
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar);
+}
+
+// Per-thread state of an epilogue thread for one tile.
+struct Epi {
+  uint8_t *A;
+  uint4 *mask;          // ReLU slope bits, [layer][column half][row]
+  uint32_t t_row;       // TMEM address of lane 32*q, column 0
+  int r, ch;            // tile row (= TMEM lane); which 128 columns
+  float px, py, pz;     // query point in the body frame
+  __device__ __forceinline__ uint4 &bits(int l) const { return mask[(l * 2 + ch) * kM + r]; }
+};
+
+// One 32-column chunk of a forward epilogue: z = D + b, h = max(z, 0); the
+// 16 packed words of the next A operand go to `w` and the slope bits are
+// returned.  The last layer adds w_out . h to fpart and writes
+// delta = [z > 0] * w_out instead of h.
+template <bool kF16, bool LAST>
+__device__ __forceinline__ uint32_t fwd_chunk(int l, int c0, const uint32_t (&raw)[32], float &fpart,
+                                              uint32_t (&w)[16]) {
+  uint32_t bits = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 b = lds4(kOffBias, (l * kW + c0) / 4 + q);
+    float4 wo = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (LAST) wo = lds4(kOffWout, c0 / 4 + q);
+    const float bv[4] = {b.x, b.y, b.z, b.w};
+    const float wv[4] = {wo.x, wo.y, wo.z, wo.w};
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float z = __uint_as_float(raw[4 * q + u]) + bv[u];
+      const bool pos = z > 0.0f;
+      bits |= (pos ? 1u : 0u) << (4 * q + u);
+      const float h = pos ? z : 0.0f;
+      if (LAST) {
+        fpart = fmaf(wv[u], h, fpart);
+        v[u] = pos ? wv[u] : 0.0f;
+      } else {
+        v[u] = h;
+      }
+    }
+    w[2 * q] = pack16<kF16>(v[0], v[1]);
+    w[2 * q + 1] = pack16<kF16>(v[2], v[3]);
+  }
+  return bits;
+}
+
+// One 32-column chunk of a reverse epilogue: delta = [z > 0] * g.
+template <bool kF16>
+__device__ __forceinline__ void bwd_chunk(uint32_t bits, const uint32_t (&raw)[32], uint32_t (&w)[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const float g0 = ((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[2 * q]) : 0.0f;
+    const float g1 = ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[2 * q + 1]) : 0.0f;
+    w[q] = pack16<kF16>(g0, g1);
+  }
+}
+
+// Forward epilogue of layer l over the thread's 128 columns (4 TMEM loads,
+// the next one issued while the current chunk is processed).
+template <bool kF16, bool LAST>
+__device__ __forceinline__ void fwd_product(const Epi &e, int l, float &fpart) {
+  const int cbase = 128 * e.ch;
+  uint32_t ra[32], rb[32], bits[4], w[16];
+  tmem_ld32_async(e.t_row + cbase, ra);
+#pragma unroll
+  for (int cc = 0; cc < 4; cc += 2) {
+    tmem_wait_ld(ra);
+    tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
+    bits[cc] = fwd_chunk<kF16, LAST>(l, cbase + 32 * cc, ra, fpart, w);
+    store_a_chunk(e.A, e.r, cbase + 32 * cc, w);
+    tmem_wait_ld(rb);
+    if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
+    bits[cc + 1] = fwd_chunk<kF16, LAST>(l, cbase + 32 * (cc + 1), rb, fpart, w);
+    store_a_chunk(e.A, e.r, cbase + 32 * (cc + 1), w);
+  }
+  if (!LAST) e.bits(l) = make_uint4(bits[0], bits[1], bits[2], bits[3]);
+}
+
+// Reverse epilogue of layer l >= 1: delta_{l-1} = [z_{l-1} > 0] * g_{l-1}.
+template <bool kF16>
+__device__ __forceinline__ void bwd_product(const Epi &e, int l) {
+  const int cbase = 128 * e.ch;
+  const uint4 m = e.bits(l - 1);
+  const uint32_t bits[4] = {m.x, m.y, m.z, m.w};
+  uint32_t ra[32], rb[32], w[16];
+  tmem_ld32_async(e.t_row + cbase, ra);
+#pragma unroll
+  for (int cc = 0; cc < 4; cc += 2) {
+    tmem_wait_ld(ra);
+    tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
+    bwd_chunk<kF16>(bits[cc], ra, w);
+    store_a_chunk(e.A, e.r, cbase + 32 * cc, w);
+    tmem_wait_ld(rb);
+    if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
+    bwd_chunk<kF16>(bits[cc + 1], rb, w);
+    store_a_chunk(e.A, e.r, cbase + 32 * (cc + 1), w);
+  }
+}
+
+// gamma(p) for the thread's 64 frequencies j = 64 ch + i: sines to columns
+// 128 ch + i, cosines to 128 ch + 64 + i.
+template <bool kF16>
+__device__ __forceinline__ void feature_stage(const Epi &e) {
+#pragma unroll 1
+  for (int cc = 0; cc < 2; ++cc) {
+    uint32_t sw[16], cw[16];
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+      const int j = 64 * e.ch + 32 * cc + i;
+      const float4 b0 = lds4(kOffFreq, j), b1 = lds4(kOffFreq, j + 1);
+      float s0, c0, s1, c1;
+      ff_sincos(b0.x, b0.y, b0.z, e.px, e.py, e.pz, s0, c0);
+      ff_sincos(b1.x, b1.y, b1.z, e.px, e.py, e.pz, s1, c1);
+      sw[i / 2] = pack16<kF16>(s0, s1);
+      cw[i / 2] = pack16<kF16>(c0, c1);
+    }
+    store_a_chunk(e.A, e.r, 128 * e.ch + 32 * cc, sw);
+    store_a_chunk(e.A, e.r, 128 * e.ch + 64 + 32 * cc, cw);
+  }
+}
+
+// Layer 0's reverse epilogue: g_gamma (in the permuted column order) through
+// the feature Jacobian, accumulated into grad f (without the factor 2 pi).
+__device__ __forceinline__ void feature_jacobian(const Epi &e, float &gx, float &gy, float &gz) {
+  const int cbase = 128 * e.ch;
+#pragma unroll 1
+  for (int cc = 0; cc < 2; ++cc) {
+    uint32_t us[32], uc[32];
+    tmem_ld32_async(e.t_row + cbase + 32 * cc, us);
+    tmem_ld32_async(e.t_row + cbase + 64 + 32 * cc, uc);
+    tmem_wait_ld(us);
+    tmem_wait_ld(uc);   // ties uc's registers to the (already complete) wait
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int j = 64 * e.ch + 32 * cc + i;
+      const float4 b = lds4(kOffFreq, j);
+      float sn, cs;
+      ff_sincos(b.x, b.y, b.z, e.px, e.py, e.pz, sn, cs);
+      const float coef = __uint_as_float(us[i]) * cs - __uint_as_float(uc[i]) * sn;
+      gx = fmaf(coef, b.x, gx);
+      gy = fmaf(coef, b.y, gy);
+      gz = fmaf(coef, b.z, gz);
+    }
+  }
+}
+
+template <bool kF16>
+__global__ void __launch_bounds__(kThreads, 1)
+    query_tc16_ff_kernel(const QueryParams prm, const __grid_constant__ CUtensorMap tmap_fwd,
+                         const __grid_constant__ CUtensorMap tmap_bwd) {
+  extern __shared__ __align__(1024) uint8_t g_smem_ff[];
+  uint8_t *smem = g_smem_ff;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if ((smem_u32(smem) & 1023u) != 0) {   // the swizzled layouts need a 1024-aligned base
+    if (threadIdx.x == 0) atomicExch(prm.err, kDevTimeout);
+    return;
+  }
+  const uint32_t sA = smem_u32(smem + kOffA), sB = smem_u32(smem + kOffB);
+  const uint32_t bar0 = smem_u32(smem + kOffBar);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
+  const uint32_t a_ready = bar0 + 8u * (2 * kStages);   // epilogue -> MMA: A written, TMEM read
+  const uint32_t d_full = a_ready + 8u;                 // MMA -> epilogue: the product is in TMEM
+  const uint32_t mma_done = d_full + 8u;
+  const uint32_t x_full = mma_done + 8u;    // columns 128..255 have published their partial sums
+  const uint32_t x_empty = x_full + 8u;     // columns 0..127 have consumed them
+  volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + kOffTmemSlot);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kOffAbort);
+  float4 *exch = reinterpret_cast<float4 *>(smem + kOffExch);
+
+  const int L = prm.n_hidden;
+  const int G = 2 * L;                         // products per tile
+  const int64_t ntiles = (prm.n + kM - 1) / kM;
+  const long long budget = prm.wait_budget;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), kCluster);   // freed when every CTA of the cluster consumed it
+    }
+    mbar_init(a_ready, kEpiWarps);
+    mbar_init(d_full, 1);
+    mbar_init(mma_done, 1);
+    mbar_init(x_full, kEpiWarps / 2);
+    mbar_init(x_empty, kEpiWarps / 2);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fence_proxy_async();
+  }
+  {
+    // biases, frequencies and w_out, once per CTA
+    float4 *dst = reinterpret_cast<float4 *>(smem + kOffBias);
+    const float4 *bsrc = reinterpret_cast<const float4 *>(prm.bias);
+    for (int i = threadIdx.x; i < L * kW / 4; i += kThreads) dst[i] = __ldg(bsrc + i);
+    dst = reinterpret_cast<float4 *>(smem + kOffFreq);
+    for (int i = threadIdx.x; i < kFreq; i += kThreads)
+      dst[i] = make_float4(__ldg(prm.ffB + 3 * i), __ldg(prm.ffB + 3 * i + 1), __ldg(prm.ffB + 3 * i + 2), 0.f);
+    dst = reinterpret_cast<float4 *>(smem + kOffWout);
+    const float4 *wosrc = reinterpret_cast<const float4 *>(prm.wout);
+    for (int i = threadIdx.x; i < kW / 4; i += kThreads) dst[i] = __ldg(wosrc + i);
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(smem + kOffTmemSlot)),
+                 "r"(kN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();      // every CTA's barriers exist before any multicast targets them
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t crank = cluster_rank();
+  const uint16_t cmask = (uint16_t)((1u << kCluster) - 1u);
+  // every CTA walks the same number of tiles (the cluster's CTAs consume the
+  // same weight panels in lockstep); tiles past the end are all-masked
+  const int64_t iters = (ntiles + gridDim.x - 1) / gridDim.x;
+
+  auto fail = [&]() {
+    atomicExch(prm.err, kDevTimeout);
+    *abort_flag = 1;
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, issued_parity = 0;   // per stage: a load in flight, its phase
+      int64_t load_idx = 0;
+      bool ok = true;
+      for (int64_t it = 0; ok && it < iters; ++it) {
+        for (int g = 0; ok && g < G; ++g) {
+          const bool fwd = g < L;
+          const int l = fwd ? g : G - 1 - g;            // network layer of this product
+          const CUtensorMap *map = fwd ? &tmap_fwd : &tmap_bwd;
+          for (int k = 0; k < kAtoms; ++k, ++load_idx) {
+            if (!mbar_wait(empty_bar(stage), phase ^ 1u, budget, abort_flag)) {
+              fail();
+              ok = false;
+              break;
+            }
+            if (load_idx != prm.drop_load) {
+              mbar_expect_tx(full_bar(stage), kStageBytes);   // both slices land here
+              tma_load_2d_mc(sB + stage * kStageBytes + crank * (kSliceRows * kKAtom * 2), map,
+                             k * kKAtom, l * kW + (int)crank * kSliceRows, full_bar(stage), cmask);
+              issued_mask |= 1u << stage;
+              issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+            }
+            if (++stage == kStages) stage = 0, phase ^= 1u;
+          }
+        }
+      }
+      // drain: every issued load must land before the CTA may exit
+      for (int s = 0; s < kStages; ++s) {
+        if (issued_mask & (1u << s)) {
+          volatile int no_abort = 0;
+          if (!mbar_wait(full_bar(s), (issued_parity >> s) & 1u, budget, &no_abort)) fail();
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(kF16, kM, kN);
+      int stage = 0;
+      uint32_t phase = 0, a_phase = 0;
+      bool ok = true;
+      for (int64_t it = 0; ok && it < iters; ++it) {
+        for (int g = 0; ok && g < G; ++g) {
+          if (!mbar_wait(a_ready, a_phase, budget, abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          a_phase ^= 1u;
+          for (int k = 0; k < kAtoms; ++k) {
+            if (!mbar_wait(full_bar(stage), phase, budget, abort_flag)) {
+              fail();
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_atom = sA + k * kAtomBytes;
+            const uint32_t b_stage = sB + stage * kStageBytes;
+#pragma unroll
+            for (int ks = 0; ks < kKAtom / 16; ++ks)
+              mma_f16(tmem, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32), idesc,
+                      (k | ks) != 0 ? 1u : 0u);
+            mma_commit_mc(empty_bar(stage), cmask);
+            if (++stage == kStages) stage = 0, phase ^= 1u;
+          }
+          if (!ok) break;
+          mma_commit(d_full);
+        }
+      }
+      // drain: no product may still be writing TMEM when it is freed
+      mma_commit(mma_done);
+      volatile int no_abort = 0;
+      if (!mbar_wait(mma_done, 0, budget, &no_abort)) fail();
+    }
+  } else if (warp >= kEpiWarp0) {
+    // ---------------- epilogue warps ----------------
+    const int q = warp & 3;                  // TMEM lane quarter
+    const int ch = (warp - kEpiWarp0) >> 2;  // columns 0..127 or 128..255
+    const int r = 32 * q + lane;             // row of the tile = TMEM lane
+    Epi e;
+    e.A = smem + kOffA;
+    e.mask = reinterpret_cast<uint4 *>(smem + kOffMask);
+    e.t_row = tmem + ((uint32_t)(32 * q) << 16);
+    e.r = r;
+    e.ch = ch;
+    uint32_t d_phase = 0, x_phase = 0;
+    bool ok = true;
+    // warp-uniform, so that no TMEM load below runs with part of a warp
+    auto wait_product = [&]() -> bool {
+      const bool got = __all_sync(0xffffffffu, mbar_wait(d_full, d_phase, budget, abort_flag));
+      d_phase ^= 1u;
+      tc_fence_after();
+      return got;
+    };
+    for (int64_t it = 0; ok && it < iters; ++it) {
+      const int64_t tile = blockIdx.x + it * gridDim.x;
+      const int64_t idx = tile * kM + r;
+      float4 pw = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (idx < prm.n) pw = prm.pts[idx];
+      e.px = pw.x; e.py = pw.y; e.pz = pw.z;
+      if (prm.has_T) {
+        const float *t = prm.Ti;
+        e.px = t[0] * pw.x + t[1] * pw.y + t[2] * pw.z + t[3];
+        e.py = t[4] * pw.x + t[5] * pw.y + t[6] * pw.z + t[7];
+        e.pz = t[8] * pw.x + t[9] * pw.y + t[10] * pw.z + t[11];
+      }
+      float fpart = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+
+      // ---- gamma(p), the first A operand ----
+      feature_stage<kF16>(e);
+      epi_arrive(a_ready, lane);
+
+      // ---- layers 0 .. L-1 (forward) ----
+      for (int l = 0; ok && l < L; ++l) {
+        if (!wait_product()) { fail(); ok = false; break; }
+        if (l == L - 1) fwd_product<kF16, true>(e, l, fpart);
+        else fwd_product<kF16, false>(e, l, fpart);
+        epi_arrive(a_ready, lane);
+      }
+      // ---- Jacobian-transpose chain: layers L-1 .. 1 ----
+      for (int l = L - 1; ok && l >= 1; --l) {
+        if (!wait_product()) { fail(); ok = false; break; }
+        bwd_product<kF16>(e, l);
+        epi_arrive(a_ready, lane);
+      }
+      if (!ok) break;
+      // ---- layer 0: g_gamma through the feature Jacobian ----
+      if (!wait_product()) { fail(); ok = false; break; }
+      feature_jacobian(e, gx, gy, gz);
+      tc_fence_before();
+      gx *= kTwoPi; gy *= kTwoPi; gz *= kTwoPi;
+
+      // ---- combine the two column halves, normalise, test, project ----
+      if (ch == 1) {
+        if (!mbar_wait(x_empty, x_phase ^ 1u, budget, abort_flag)) { fail(); ok = false; break; }
+        exch[r] = make_float4(gx, gy, gz, fpart);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(x_full);
+        x_phase ^= 1u;
+        continue;
+      }
+      if (!mbar_wait(x_full, x_phase, budget, abort_flag)) { fail(); ok = false; break; }
+      x_phase ^= 1u;
+      const float4 o = exch[r];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(x_empty);
+      if (idx < prm.n) {
+        gx += o.x; gy += o.y; gz += o.z;
+        const float f = fpart + o.w + __ldg(prm.bout);
+        const float nrm = sqrtf(gx * gx + gy * gy + gz * gz);
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (nrm >= 1e-20f) { nx = gx / nrm; ny = gy / nrm; nz = gz / nrm; }
+        if (!prm.collide) {
+          if (prm.raw_gradient) { nx = gx; ny = gy; nz = gz; }
+          prm.out_n_sdf[idx] = make_float4(nx, ny, nz, f);
+        } else {
+          if (prm.has_T) {
+            const float *R = prm.R;
+            const float wx = R[0] * nx + R[1] * ny + R[2] * nz;
+            const float wy = R[3] * nx + R[4] * ny + R[5] * nz;
+            const float wz = R[6] * nx + R[7] * ny + R[8] * nz;
+            nx = wx; ny = wy; nz = wz;
+          }
+          const bool hit = f < prm.eps;
+          float4 p = pw;
+          if (hit) {
+            const float d = prm.eps - f;
+            p.x = fmaf(d, nx, p.x); p.y = fmaf(d, ny, p.y); p.z = fmaf(d, nz, p.z);
+          }
+          if (prm.out_pts) prm.out_pts[idx] = p;
+          if (prm.out_n_sdf) prm.out_n_sdf[idx] = make_float4(nx, ny, nz, f);
+          if (prm.out_hit) prm.out_hit[idx] = hit ? 1 : 0;
+        }
+      }
+    }
+  }
+  // every warp ends here: all TMEM traffic is done before the owner frees it,
+  // and no CTA leaves while a cluster peer may still multicast into it
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kN));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// [rows x 256] 16-bit panels, boxes of 64 columns x kSliceRows rows.
+bool encode_map(CUtensorMap *map, void *base, int rows, bool fp16) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kW, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kW * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kKAtom, (cuuint32_t)kSliceRows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// CTAs that can be resident at once in whole clusters.
+int resident_cluster_ctas(int num_sms) {
+  static int cached[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev] < num_sms ? cached[dev] : num_sms;
+  cudaFuncSetAttribute(query_tc16_ff_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCluster * 256, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, query_tc16_ff_kernel<false>, &cfg) != cudaSuccess ||
+      clusters < 1) {
+    cudaGetLastError();
+    clusters = num_sms / kCluster;
+  }
+  const int ctas = clusters * kCluster;
+  if (dev >= 0 && dev < 64) cached[dev] = ctas;
+  return ctas < num_sms ? ctas : num_sms;
+}
+
+template <bool kF16>
+cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(query_tc16_ff_kernel<kF16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  const int grid = query_tc16_ff_grid(p.n, num_sms);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, query_tc16_ff_kernel<kF16>, p, net.tmap_fwd, net.tmap_bwd);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool query_tc16_ff_supported(int width, int n_hidden, int ff, int relu) {
+  return width == kW && ff == kFreq && relu != 0 && n_hidden >= 1 && n_hidden <= kMaxHidden;
+}
+
+bool make_tc16_ff_tmaps(NetDevice &net, int n_hidden, bool fp16) {
+  if (n_hidden < 1 || n_hidden > kMaxHidden) return false;
+  const int rows = n_hidden * kW;
+  return encode_map(&net.tmap_fwd, net.fwd16, rows, fp16) &&
+         encode_map(&net.tmap_bwd, net.bwd16, rows, fp16);
+}
+
+int query_tc16_ff_grid(int64_t n, int num_sms) {
+  const int64_t tiles = (n + kM - 1) / kM;
+  const int cap = resident_cluster_ctas(num_sms);
+  int64_t g = tiles < cap ? tiles : cap;
+  g = (g / kCluster) * kCluster;                 // whole clusters
+  return (int)(g < kCluster ? kCluster : g);
+}
+
+cudaError_t launch_query_tc16_ff(const QueryParams &p, const NetDevice &net, bool fp16, int num_sms,
+                                 cudaStream_t s) {
+  if (!query_tc16_ff_supported(p.width, p.n_hidden, p.ff, p.relu)) return cudaErrorInvalidValue;
+  return fp16 ? launch_t<true>(p, net, num_sms, s) : launch_t<false>(p, net, num_sms, s);
+}
+
+}  // namespace nsdf

@@ -268,6 +268,7 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
   nsdf_status st = ctx_query_setup(ctx, &p, &num_sms, &W, &L, &tc16, &fp16, &net);
   if (st != NSDF_OK) return st;
   if (!tc16) return NSDF_ERR_UNSUPPORTED;   // FP32 contexts: nsdf_backward
+  if (p.ff > 0 || p.relu) return NSDF_ERR_UNSUPPORTED;   // softplus networks only
   if (n == 0) return NSDF_ERR_INVALID_ARG;
   if (!pts || !targets) return NSDF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(pts) & 15u) || (reinterpret_cast<uintptr_t>(g_weights) & 3u) ||

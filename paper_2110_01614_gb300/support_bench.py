@@ -13,9 +13,10 @@
 
 * paper_arch: the paper's own network shapes (Sec. 4.3: a Fourier-feature
   layer of 128 frequencies, then 8 (dragon) or 4 (bunny) ReLU layers of 256
-  units), collision query of 1,048,576 body-scale points in the FP32 kernel;
-  the paper's Table 1 quotes 255 ms / 350 ms for 1M queries on a Tesla T4
-  (context only: other hardware, other weights).
+  units), collision query of 1,048,576 body-scale points in the FP32 kernel
+  and in the BF16 / FP16 tensor-core kernel; the paper's Table 1 quotes
+  255 ms / 350 ms for 1M queries on a Tesla T4 (context only: other
+  hardware, other weights).
 
 * fit512: the 512-wide body-scale network fitted with the paper's L1 loss on
   the BF16 tensor-core path (pool of 1,048,576 points with exact targets,
@@ -129,21 +130,24 @@ def bench_cloth(steps=20):
 
 
 def bench_paper_arch(reps=10):
-    res = {"workload": "paper_arch", "points": 1 << 20, "precision": "fp32"}
+    res = {"workload": "paper_arch", "points": 1 << 20}
     pts = torch.from_numpy(synth.body_scale_points(1 << 20, 1)).cuda()
     out, ns = torch.empty_like(pts), torch.empty_like(pts)
     for name, L in (("dragon_8x256", 8), ("bunny_4x256", 4)):
         arch = synth.Arch(3, 256, L, -1, 100.0, "relu", 128)
-        net = NeuralSDF(arch, NSDF_FP32).load(synth.fourier_relu_init(arch, 0))
-        net.collide(pts, 0.002, out_pts=out, out_n_sdf=ns)
-        ms = events_ms(lambda: net.collide(pts, 0.002, out_pts=out, out_n_sdf=ns), reps)
-        nsdf_sync_status(net.ctx)
-        net.close()
+        blob = synth.fourier_relu_init(arch, 0)
         # algorithmic MAC per query: L0 and L-1 hidden 256x256 products forward,
         # the same transposed backward (incl. W_0^T), plus the output unit
         mac = 2 * L * 256 * 256 + 256
-        res[name] = {"ms": ms, "queries_per_s": (1 << 20) / (ms * 1e-3),
-                     "tflops": 2 * mac * (1 << 20) / (ms * 1e-3) / 1e12}
+        res[name] = {}
+        for prec, pname in ((NSDF_FP32, "fp32"), (NSDF_BF16, "bf16"), (NSDF_FP16, "fp16")):
+            net = NeuralSDF(arch, prec).load(blob)
+            net.collide(pts, 0.002, out_pts=out, out_n_sdf=ns)
+            ms = events_ms(lambda: net.collide(pts, 0.002, out_pts=out, out_n_sdf=ns), reps)
+            nsdf_sync_status(net.ctx)
+            net.close()
+            res[name][pname] = {"ms": ms, "queries_per_s": (1 << 20) / (ms * 1e-3),
+                                "tflops": 2 * mac * (1 << 20) / (ms * 1e-3) / 1e12}
     return res
 
 

@@ -1,0 +1,186 @@
+"""GPU parity of the 16-bit tensor-core kernel for the paper's own networks
+(Sec. 4.3: a Fourier-feature layer of 128 frequencies, then 8 or 4 ReLU
+layers of 256 units) against the oracles.
+
+Two references, because a ReLU slope is a decision taken by floating point:
+
+* ``oracle.rounded.query_ff_relu`` evaluates the network with the
+  tensor-core operands rounded to the kernel's 16-bit format (features,
+  weights, activations, deltas) and takes the ReLU decisions in that
+  precision.  It differs from the kernel only by the order and precision of
+  the accumulation (FP32 in the kernel, exact here) and by what that order
+  changes downstream: an activation that lands on the other side of a
+  16-bit rounding boundary, and, rarely, a ReLU decision with |z| below
+  that difference.  Re-running the rounded oracle with every product
+  accumulated in FP32 moves its f by at most 2.9 u (BF16) and 4.7 u (FP16)
+  on the 8-layer network, 99% of points by under 2.7 u (u = unit roundoff
+  of the format: 2^-9 BF16, 2^-12 FP16).  So f must agree within 8 u, and
+  within 4 u at the 99th percentile; the normal within 1e-3 rad at 90% of
+  the points and within 1e-2 rad at 97%.
+* ``oracle.mlp`` is exact.  f is continuous through the ReLU kinks, so its
+  error is bounded by the rounding alone: the rounded oracle is within 16 u
+  of it (tests/test_oracle_rounded.py), so the kernel must be within 24 u.
+  The collision decision f < eps must agree wherever |f - eps| > 24 u.  The
+  exact normal is not compared point by point: with randomly initialised
+  ReLU weights each decision flip moves it by a large angle (see the
+  oracle's module docstring).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import mlp, rounded
+from parity import normal_angle
+
+pytestmark = pytest.mark.gpu
+
+DRAGON = synth.Arch(3, 256, 8, -1, 100.0, "relu", 128)
+BUNNY = synth.Arch(3, 256, 4, -1, 100.0, "relu", 128)
+SHALLOW = synth.Arch(3, 256, 1, -1, 100.0, "relu", 128)
+EPS = 0.002
+U = {"bf16": 2.0 ** -9, "fp16": 2.0 ** -12}
+
+
+@pytest.fixture(scope="module")
+def nsdf(nsdf_lib):
+    import paper_2110_01614_gb300 as m
+    return m
+
+
+def P(nsdf, fmt):
+    return nsdf.NSDF_FP16 if fmt == "fp16" else nsdf.NSDF_BF16
+
+
+def collide_gpu(nsdf, fmt, arch, blob, pts, T=None, noalloc=False):
+    s = nsdf.NeuralSDF(arch, P(nsdf, fmt)).load(blob)
+    d = torch.from_numpy(pts).cuda()
+    out_pts, out_ns = torch.empty_like(d), torch.empty_like(d)
+    hit = torch.empty(len(pts), dtype=torch.uint8, device="cuda")
+    if noalloc:
+        nsdf.nsdf_collide_noalloc(s.ctx, d, EPS, out_pts, out_ns, hit, T=T)
+    else:
+        s.collide(d, EPS, T=T, out_pts=out_pts, out_n_sdf=out_ns, out_hit=hit)
+    nsdf.nsdf_sync_status(s.ctx)
+    s.close()
+    return out_pts.cpu().numpy(), out_ns.cpu().numpy(), hit.cpu().numpy()
+
+
+def check(fmt, arch, blob, pts, out, ns, hit, T=None):
+    """Every bound of the module docstring; returns the error statistics."""
+    u = U[fmt]
+    local = pts[:, :3].astype(np.float64)
+    if T is not None:
+        Ti = np.linalg.inv(np.asarray(T, dtype=np.float64))
+        local = local @ Ti[:3, :3].T + Ti[:3, 3]
+    f_r, g_r, _ = rounded.query_ff_relu(blob, arch, local, fmt)
+    f_x, N_x, hit_x, _ = mlp.collide(blob, arch, pts, EPS, T=T)
+    n_r = g_r / np.linalg.norm(g_r, axis=1, keepdims=True)
+    if T is not None:
+        n_r = n_r @ np.asarray(T, dtype=np.float64)[:3, :3].T
+    f = ns[:, 3].astype(np.float64)
+    ang = normal_angle(n_r, ns[:, :3])
+    dr = np.abs(f - f_r) / u
+    stats = {"f_vs_rounded": float(dr.max()), "f_vs_rounded_p99": float(np.percentile(dr, 99)),
+             "f_vs_exact": float(np.abs(f - f_x).max() / u),
+             "ang_med": float(np.median(ang)), "within_1e-3": float(np.mean(ang <= 1e-3)),
+             "within_1e-2": float(np.mean(ang <= 1e-2))}
+    print(fmt, arch.n_hidden, {k: round(v, 6) for k, v in stats.items()})
+    assert stats["f_vs_rounded"] <= 8.0, stats
+    assert stats["f_vs_rounded_p99"] <= 4.0, stats
+    assert stats["f_vs_exact"] <= 24.0, stats
+    assert stats["within_1e-3"] >= 0.90, stats
+    assert stats["within_1e-2"] >= 0.97, stats
+    far = np.abs(f_x - EPS) > 24 * u
+    np.testing.assert_array_equal(hit[far], hit_x[far])
+    # the contact point of Eq. 3 from the kernel's own f and N
+    exp = pts[:, :3] + np.where(hit[:, None] == 1, (EPS - f)[:, None] * ns[:, :3], 0.0)
+    np.testing.assert_allclose(out[:, :3], exp, atol=2e-6)
+    return stats
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+@pytest.mark.parametrize("arch", [DRAGON, BUNNY], ids=["8x256", "4x256"])
+def test_matches_oracles(nsdf, fmt, arch):
+    blob = synth.fourier_relu_init(arch, 0)
+    pts = synth.body_scale_points(4096, 1)
+    out, ns, hit = collide_gpu(nsdf, fmt, arch, blob, pts)
+    check(fmt, arch, blob, pts, out, ns, hit)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_pose_and_ragged_tail(nsdf, fmt):
+    """A posed body (Sec. 4.2) and 1037 points: eight full tiles and a tail of 13."""
+    blob = synth.fourier_relu_init(BUNNY, 3)
+    pts = synth.uniform_cube_points(1037, 4)
+    T = synth.rigid_transforms(1, seed=12)[0]
+    out, ns, hit = collide_gpu(nsdf, fmt, BUNNY, blob, pts, T=T)
+    check(fmt, BUNNY, blob, pts, out, ns, hit, T=T)
+
+
+def test_single_layer_network(nsdf):
+    """n_hidden = 1: the Fourier-feature layer is the only hidden layer, so
+    the forward pass is one product and the reverse chain goes straight from
+    w_out through W_0 into the feature Jacobian."""
+    blob = synth.fourier_relu_init(SHALLOW, 5)
+    pts = synth.body_scale_points(700, 6)
+    out, ns, hit = collide_gpu(nsdf, "bf16", SHALLOW, blob, pts)
+    check("bf16", SHALLOW, blob, pts, out, ns, hit)
+
+
+def test_raw_gradient_query(nsdf):
+    """Query mode with NSDF_RAW_GRADIENT returns grad f itself."""
+    blob = synth.fourier_relu_init(BUNNY, 7)
+    pts = synth.uniform_cube_points(2000, 8)
+    s = nsdf.NeuralSDF(BUNNY, nsdf.NSDF_FP16).load(blob)
+    d = torch.from_numpy(pts).cuda()
+    raw = s.query(d, raw_gradient=True).cpu().numpy()
+    unit = s.query(d).cpu().numpy()
+    nsdf.nsdf_sync_status(s.ctx)
+    s.close()
+    f_r, g_r, _ = rounded.query_ff_relu(blob, BUNNY, pts[:, :3].astype(np.float64), "fp16")
+    rel = np.linalg.norm(raw[:, :3] - g_r, axis=1) / np.linalg.norm(g_r, axis=1)
+    assert np.mean(rel <= 1e-3) >= 0.9
+    np.testing.assert_allclose(unit[:, 3], raw[:, 3], rtol=0, atol=0)
+    nrm = raw[:, :3] / np.linalg.norm(raw[:, :3], axis=1, keepdims=True)
+    np.testing.assert_allclose(unit[:, :3], nrm, atol=1e-6)
+
+
+def test_allocation_free_entry_point(nsdf):
+    blob = synth.fourier_relu_init(DRAGON, 9)
+    pts = synth.body_scale_points(3000, 10)
+    a = collide_gpu(nsdf, "bf16", DRAGON, blob, pts)
+    b = collide_gpu(nsdf, "bf16", DRAGON, blob, pts, noalloc=True)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_full_size_sampled(nsdf):
+    """1,048,576 body-scale points (the paper's 1M-point query) through the
+    dragon-shaped network in BF16; 4096 sampled points against the oracles."""
+    blob = synth.fourier_relu_init(DRAGON, 0)
+    pts = synth.body_scale_points(1 << 20, 1)
+    out, ns, hit = collide_gpu(nsdf, "bf16", DRAGON, blob, pts)
+    idx = np.unique(synth.Stream(77).u64(4096) % np.uint64(len(pts))).astype(np.int64)
+    check("bf16", DRAGON, blob, pts[idx], out[idx], ns[idx], hit[idx])
+
+
+def test_unsupported_shapes_are_refused(nsdf):
+    """The 16-bit kernels take Fourier-feature ReLU networks of width 256 with
+    1..8 layers, and softplus networks of width 512; anything else is refused
+    at creation."""
+    for arch in (synth.Arch(3, 128, 4, -1, 100.0, "relu", 64),      # other width
+                 synth.Arch(3, 256, 9, -1, 100.0, "relu", 128),     # too deep
+                 synth.Arch(3, 256, 4, -1, 100.0, "relu", 0),       # ReLU without features
+                 synth.Arch(3, 256, 4, -1, 100.0, "softplus", 128)):
+        with pytest.raises(nsdf.NsdfError):
+            nsdf.NeuralSDF(arch, nsdf.NSDF_BF16)
+
+
+def test_empty_input(nsdf):
+    s = nsdf.NeuralSDF(BUNNY, nsdf.NSDF_BF16).load(synth.fourier_relu_init(BUNNY, 0))
+    d = torch.empty((0, 4), dtype=torch.float32, device="cuda")
+    s.collide(d, EPS, out_pts=torch.empty_like(d))
+    nsdf.nsdf_sync_status(s.ctx)
+    s.close()
