@@ -71,19 +71,20 @@ constexpr int kAtomBytes = kM * kKAtom * 2;      // 16 KB: one K atom of A
 constexpr int kEpiWarps = 8;
 constexpr int kEpiWarp0 = 4;
 constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
-constexpr float kTwoPi = 6.28318530717958648f;
+constexpr float kPi = 3.14159265358979324f;
 
 // shared-memory map (bytes from a 1024-aligned base)
 constexpr int kOffA = 0;
 constexpr int kOffB = kOffA + kABytes;
 constexpr int kOffMask = kOffB + kStages * kStageBytes;          // uint4 [kMaxHidden-1][2][kM]
 constexpr int kOffBias = kOffMask + (kMaxHidden - 1) * 2 * kM * 16;   // float [kMaxHidden][kW]
-constexpr int kOffFreq = kOffBias + kMaxHidden * kW * 4;         // float4 [kFreq]: b_j
+constexpr int kOffFreq = kOffBias + kMaxHidden * kW * 4;         // float4 [kFreq]: 2 b_j
 constexpr int kOffWout = kOffFreq + kFreq * 16;                  // float [kW]
 constexpr int kOffExch = kOffWout + kW * 4;                      // float4 [kM]
 constexpr int kOffBar = kOffExch + kM * 16;
-// barriers: full[kStages], empty[kStages], a_ready, d_full, mma_done, x_full, x_empty
-constexpr int kNumBars = 2 * kStages + 5;
+// barriers: full[kStages], empty[kStages], a_ready[kAtoms], d_full, mma_done, x_full, x_empty
+constexpr int kNumBars = 2 * kStages + kAtoms + 4;
+constexpr int kTmemCols = 2 * kN;                 // two products in flight
 constexpr int kOffTmemSlot = kOffBar + 8 * kNumBars;
 constexpr int kOffAbort = kOffTmemSlot + 4;
 constexpr int kSmemBytes = kOffAbort + 4;
@@ -107,9 +108,10 @@ __device__ __forceinline__ void epi_arrive(uint32_t bar, int lane) {
 // Per-thread state of an epilogue thread for one tile.
 struct Epi {
   uint8_t *A;
-  uint4 *mask;          // ReLU slope bits, [layer][column half][row]
+  uint4 *mask;          // ReLU slope bits, [layer][column group][row]
   uint32_t t_row;       // TMEM address of lane 32*q, column 0
-  int r, ch;            // tile row (= TMEM lane); which 128 columns
+  uint32_t a_ready;     // barrier a_ready[0]; a_ready[k] is 8 k bytes on
+  int r, ch, lane;      // tile row (= TMEM lane); column group (32 of every atom)
   float px, py, pz;     // query point in the body frame
   __device__ __forceinline__ uint4 &bits(int l) const { return mask[(l * 2 + ch) * kM + r]; }
 };
@@ -160,87 +162,102 @@ __device__ __forceinline__ void bwd_chunk(uint32_t bits, const uint32_t (&raw)[3
   }
 }
 
-// Forward epilogue of layer l over the thread's 128 columns (4 TMEM loads,
-// the next one issued while the current chunk is processed).
+// Columns of chunk k (0..3) of this thread: 32 columns of K atom k.  Both
+// column groups work through the atoms in order, so atom k of the next A
+// operand is complete, and announced on a_ready[k], after a quarter of the
+// epilogue, and the next product starts on it while the rest is written.
+__device__ __forceinline__ int chunk_col(const Epi &e, int k) { return 64 * k + 32 * e.ch; }
+
+// Forward epilogue of layer l, product in TMEM columns dcol..dcol+255 (the
+// next chunk's TMEM load is issued while the current one is processed).
 template <bool kF16, bool LAST>
-__device__ __forceinline__ void fwd_product(const Epi &e, int l, float &fpart) {
-  const int cbase = 128 * e.ch;
+__device__ __forceinline__ void fwd_product(const Epi &e, int l, uint32_t dcol, float &fpart) {
+  const uint32_t t = e.t_row + dcol;
   uint32_t ra[32], rb[32], bits[4], w[16];
-  tmem_ld32_async(e.t_row + cbase, ra);
+  tmem_ld32_async(t + chunk_col(e, 0), ra);
 #pragma unroll
-  for (int cc = 0; cc < 4; cc += 2) {
+  for (int k = 0; k < 4; k += 2) {
     tmem_wait_ld(ra);
-    tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
-    bits[cc] = fwd_chunk<kF16, LAST>(l, cbase + 32 * cc, ra, fpart, w);
-    store_a_chunk(e.A, e.r, cbase + 32 * cc, w);
+    tmem_ld32_async(t + chunk_col(e, k + 1), rb);
+    bits[k] = fwd_chunk<kF16, LAST>(l, chunk_col(e, k), ra, fpart, w);
+    store_a_chunk(e.A, e.r, chunk_col(e, k), w);
+    epi_arrive(e.a_ready + 8u * k, e.lane);
     tmem_wait_ld(rb);
-    if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
-    bits[cc + 1] = fwd_chunk<kF16, LAST>(l, cbase + 32 * (cc + 1), rb, fpart, w);
-    store_a_chunk(e.A, e.r, cbase + 32 * (cc + 1), w);
+    if (k + 2 < 4) tmem_ld32_async(t + chunk_col(e, k + 2), ra);
+    bits[k + 1] = fwd_chunk<kF16, LAST>(l, chunk_col(e, k + 1), rb, fpart, w);
+    store_a_chunk(e.A, e.r, chunk_col(e, k + 1), w);
+    epi_arrive(e.a_ready + 8u * (k + 1), e.lane);
   }
   if (!LAST) e.bits(l) = make_uint4(bits[0], bits[1], bits[2], bits[3]);
 }
 
 // Reverse epilogue of layer l >= 1: delta_{l-1} = [z_{l-1} > 0] * g_{l-1}.
 template <bool kF16>
-__device__ __forceinline__ void bwd_product(const Epi &e, int l) {
-  const int cbase = 128 * e.ch;
+__device__ __forceinline__ void bwd_product(const Epi &e, int l, uint32_t dcol) {
+  const uint32_t t = e.t_row + dcol;
   const uint4 m = e.bits(l - 1);
   const uint32_t bits[4] = {m.x, m.y, m.z, m.w};
   uint32_t ra[32], rb[32], w[16];
-  tmem_ld32_async(e.t_row + cbase, ra);
+  tmem_ld32_async(t + chunk_col(e, 0), ra);
 #pragma unroll
-  for (int cc = 0; cc < 4; cc += 2) {
+  for (int k = 0; k < 4; k += 2) {
     tmem_wait_ld(ra);
-    tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
-    bwd_chunk<kF16>(bits[cc], ra, w);
-    store_a_chunk(e.A, e.r, cbase + 32 * cc, w);
+    tmem_ld32_async(t + chunk_col(e, k + 1), rb);
+    bwd_chunk<kF16>(bits[k], ra, w);
+    store_a_chunk(e.A, e.r, chunk_col(e, k), w);
+    epi_arrive(e.a_ready + 8u * k, e.lane);
     tmem_wait_ld(rb);
-    if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
-    bwd_chunk<kF16>(bits[cc + 1], rb, w);
-    store_a_chunk(e.A, e.r, cbase + 32 * (cc + 1), w);
+    if (k + 2 < 4) tmem_ld32_async(t + chunk_col(e, k + 2), ra);
+    bwd_chunk<kF16>(bits[k + 1], rb, w);
+    store_a_chunk(e.A, e.r, chunk_col(e, k + 1), w);
+    epi_arrive(e.a_ready + 8u * (k + 1), e.lane);
   }
 }
 
-// gamma(p) for the thread's 64 frequencies j = 64 ch + i: sines to columns
-// 128 ch + i, cosines to 128 ch + 64 + i.
+// gamma(p) for the thread's 64 frequencies j = 64 blk + 32 ch + i: in the
+// permuted column order their sines are chunk 2 blk and their cosines chunk
+// 2 blk + 1 of this thread.
 template <bool kF16>
 __device__ __forceinline__ void feature_stage(const Epi &e) {
 #pragma unroll 1
-  for (int cc = 0; cc < 2; ++cc) {
+  for (int blk = 0; blk < 2; ++blk) {
     uint32_t sw[16], cw[16];
 #pragma unroll
     for (int i = 0; i < 32; i += 2) {
-      const int j = 64 * e.ch + 32 * cc + i;
+      const int j = 64 * blk + 32 * e.ch + i;
       const float4 b0 = lds4(kOffFreq, j), b1 = lds4(kOffFreq, j + 1);
       float s0, c0, s1, c1;
-      ff_sincos(b0.x, b0.y, b0.z, e.px, e.py, e.pz, s0, c0);
-      ff_sincos(b1.x, b1.y, b1.z, e.px, e.py, e.pz, s1, c1);
+      ff_sincos16(b0.x, b0.y, b0.z, e.px, e.py, e.pz, s0, c0);
+      ff_sincos16(b1.x, b1.y, b1.z, e.px, e.py, e.pz, s1, c1);
       sw[i / 2] = pack16<kF16>(s0, s1);
       cw[i / 2] = pack16<kF16>(c0, c1);
     }
-    store_a_chunk(e.A, e.r, 128 * e.ch + 32 * cc, sw);
-    store_a_chunk(e.A, e.r, 128 * e.ch + 64 + 32 * cc, cw);
+    store_a_chunk(e.A, e.r, chunk_col(e, 2 * blk), sw);
+    epi_arrive(e.a_ready + 16u * blk, e.lane);
+    store_a_chunk(e.A, e.r, chunk_col(e, 2 * blk + 1), cw);
+    epi_arrive(e.a_ready + 16u * blk + 8u, e.lane);
   }
 }
 
-// Layer 0's reverse epilogue: g_gamma (in the permuted column order) through
-// the feature Jacobian, accumulated into grad f (without the factor 2 pi).
-__device__ __forceinline__ void feature_jacobian(const Epi &e, float &gx, float &gy, float &gz) {
-  const int cbase = 128 * e.ch;
+// Layer 0's reverse epilogue: g_gamma (sine and cosine parts of the thread's
+// frequencies in chunks 2 blk and 2 blk + 1) through the feature Jacobian,
+// accumulated into grad f / pi (the table holds 2 b_j).
+__device__ __forceinline__ void feature_jacobian(const Epi &e, uint32_t dcol, float &gx, float &gy,
+                                                 float &gz) {
+  const uint32_t t = e.t_row + dcol;
 #pragma unroll 1
-  for (int cc = 0; cc < 2; ++cc) {
+  for (int blk = 0; blk < 2; ++blk) {
     uint32_t us[32], uc[32];
-    tmem_ld32_async(e.t_row + cbase + 32 * cc, us);
-    tmem_ld32_async(e.t_row + cbase + 64 + 32 * cc, uc);
+    tmem_ld32_async(t + chunk_col(e, 2 * blk), us);
+    tmem_ld32_async(t + chunk_col(e, 2 * blk + 1), uc);
     tmem_wait_ld(us);
     tmem_wait_ld(uc);   // ties uc's registers to the (already complete) wait
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
-      const int j = 64 * e.ch + 32 * cc + i;
+      const int j = 64 * blk + 32 * e.ch + i;
       const float4 b = lds4(kOffFreq, j);
       float sn, cs;
-      ff_sincos(b.x, b.y, b.z, e.px, e.py, e.pz, sn, cs);
+      ff_sincos16(b.x, b.y, b.z, e.px, e.py, e.pz, sn, cs);
       const float coef = __uint_as_float(us[i]) * cs - __uint_as_float(uc[i]) * sn;
       gx = fmaf(coef, b.x, gx);
       gy = fmaf(coef, b.y, gy);
@@ -264,8 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t bar0 = smem_u32(smem + kOffBar);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
-  const uint32_t a_ready = bar0 + 8u * (2 * kStages);   // epilogue -> MMA: A written, TMEM read
-  const uint32_t d_full = a_ready + 8u;                 // MMA -> epilogue: the product is in TMEM
+  // epilogue -> MMA: K atom k of A written (and the chunks before it read from TMEM)
+  const uint32_t a_ready = bar0 + 8u * (2 * kStages);
+  const uint32_t d_full = a_ready + 8u * kAtoms;        // MMA -> epilogue: the product is in TMEM
   const uint32_t mma_done = d_full + 8u;
   const uint32_t x_full = mma_done + 8u;    // columns 128..255 have published their partial sums
   const uint32_t x_empty = x_full + 8u;     // columns 0..127 have consumed them
@@ -283,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), kCluster);   // freed when every CTA of the cluster consumed it
     }
-    mbar_init(a_ready, kEpiWarps);
+    for (int k = 0; k < kAtoms; ++k) mbar_init(a_ready + 8u * k, kEpiWarps);
     mbar_init(d_full, 1);
     mbar_init(mma_done, 1);
     mbar_init(x_full, kEpiWarps / 2);
@@ -299,7 +317,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = threadIdx.x; i < L * kW / 4; i += kThreads) dst[i] = __ldg(bsrc + i);
     dst = reinterpret_cast<float4 *>(smem + kOffFreq);
     for (int i = threadIdx.x; i < kFreq; i += kThreads)
-      dst[i] = make_float4(__ldg(prm.ffB + 3 * i), __ldg(prm.ffB + 3 * i + 1), __ldg(prm.ffB + 3 * i + 2), 0.f);
+      dst[i] = make_float4(2.f * __ldg(prm.ffB + 3 * i), 2.f * __ldg(prm.ffB + 3 * i + 1),
+                           2.f * __ldg(prm.ffB + 3 * i + 2), 0.f);
     dst = reinterpret_cast<float4 *>(smem + kOffWout);
     const float4 *wosrc = reinterpret_cast<const float4 *>(prm.wout);
     for (int i = threadIdx.x; i < kW / 4; i += kThreads) dst[i] = __ldg(wosrc + i);
@@ -307,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      smem_u32(smem + kOffTmemSlot)),
-                 "r"(kN));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   tc_fence_before();
@@ -373,15 +392,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int64_t it = 0; ok && it < iters; ++it) {
         for (int g = 0; ok && g < G; ++g) {
-          if (!mbar_wait(a_ready, a_phase, budget, abort_flag)) {
-            fail();
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          a_phase ^= 1u;
+          const uint32_t d = tmem + (uint32_t)(kN * (g & 1));   // products alternate buffers
           for (int k = 0; k < kAtoms; ++k) {
-            if (!mbar_wait(full_bar(stage), phase, budget, abort_flag)) {
+            if (!mbar_wait(a_ready + 8u * k, a_phase, budget, abort_flag) ||
+                !mbar_wait(full_bar(stage), phase, budget, abort_flag)) {
               fail();
               ok = false;
               break;
@@ -391,12 +405,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t b_stage = sB + stage * kStageBytes;
 #pragma unroll
             for (int ks = 0; ks < kKAtom / 16; ++ks)
-              mma_f16(tmem, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32), idesc,
+              mma_f16(d, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32), idesc,
                       (k | ks) != 0 ? 1u : 0u);
             mma_commit_mc(empty_bar(stage), cmask);
             if (++stage == kStages) stage = 0, phase ^= 1u;
           }
           if (!ok) break;
+          a_phase ^= 1u;
           mma_commit(d_full);
         }
       }
@@ -414,8 +429,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     e.A = smem + kOffA;
     e.mask = reinterpret_cast<uint4 *>(smem + kOffMask);
     e.t_row = tmem + ((uint32_t)(32 * q) << 16);
+    e.a_ready = a_ready;
     e.r = r;
     e.ch = ch;
+    e.lane = lane;
     uint32_t d_phase = 0, x_phase = 0;
     bool ok = true;
     // warp-uniform, so that no TMEM load below runs with part of a warp
@@ -439,29 +456,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       float fpart = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 
+      // product g of the tile sits in TMEM columns kN * (g % 2) ..
+      auto dcol = [](int g) { return (uint32_t)(kN * (g & 1)); };
+
       // ---- gamma(p), the first A operand ----
       feature_stage<kF16>(e);
-      epi_arrive(a_ready, lane);
 
-      // ---- layers 0 .. L-1 (forward) ----
+      // ---- layers 0 .. L-1 (forward): product l ----
       for (int l = 0; ok && l < L; ++l) {
         if (!wait_product()) { fail(); ok = false; break; }
-        if (l == L - 1) fwd_product<kF16, true>(e, l, fpart);
-        else fwd_product<kF16, false>(e, l, fpart);
-        epi_arrive(a_ready, lane);
+        if (l == L - 1) fwd_product<kF16, true>(e, l, dcol(l), fpart);
+        else fwd_product<kF16, false>(e, l, dcol(l), fpart);
       }
-      // ---- Jacobian-transpose chain: layers L-1 .. 1 ----
+      // ---- Jacobian-transpose chain: layers L-1 .. 1, product 2L-1-l ----
       for (int l = L - 1; ok && l >= 1; --l) {
         if (!wait_product()) { fail(); ok = false; break; }
-        bwd_product<kF16>(e, l);
-        epi_arrive(a_ready, lane);
+        bwd_product<kF16>(e, l, dcol(G - 1 - l));
       }
       if (!ok) break;
-      // ---- layer 0: g_gamma through the feature Jacobian ----
+      // ---- layer 0 (product 2L-1): g_gamma through the feature Jacobian ----
       if (!wait_product()) { fail(); ok = false; break; }
-      feature_jacobian(e, gx, gy, gz);
+      feature_jacobian(e, dcol(G - 1), gx, gy, gz);
       tc_fence_before();
-      gx *= kTwoPi; gy *= kTwoPi; gz *= kTwoPi;
+      gx *= kPi; gy *= kPi; gz *= kPi;
 
       // ---- combine the two column halves, normalise, test, project ----
       if (ch == 1) {
@@ -514,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
   }
 }
 
