@@ -228,7 +228,7 @@ int query_grid(const nsdf_ctx *ctx, int64_t n) {
 }
 
 size_t query_scratch(const nsdf_ctx *ctx, int grid) {
-  if (use_tc16_ff(ctx)) return 0;
+  if (use_tc16_ff(ctx)) return query_tc16_ff_scratch_bytes(grid);
   if (use_bf16(ctx)) return query_tc16_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
   return query_fp32_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
 }

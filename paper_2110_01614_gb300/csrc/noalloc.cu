@@ -85,7 +85,12 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   p.out_pts = reinterpret_cast<float4 *>(out_pts);
   p.out_n_sdf = reinterpret_cast<float4 *>(out_n_sdf);
   p.out_hit = out_hit;
-  if (tc16 && p.ff > 0) {   // the Fourier-feature tensor-core kernel needs no scratch
+  if (tc16 && p.ff > 0) {   // Fourier-feature tensor-core kernel: one slope-bit slab per CTA
+    const int grid = query_tc16_ff_grid(n, num_sms);
+    if (query_tc16_ff_scratch_bytes(grid) > kNoAllocScratchBytes) return NSDF_ERR_TOO_LARGE;
+    void *scratch = nullptr;
+    if (scratch_address(&scratch) != cudaSuccess) return NSDF_ERR_CUDA;
+    p.scratch = static_cast<float *>(scratch);
     const cudaError_t e = launch_query_tc16_ff(p, *net, fp16, num_sms, s);
     return e == cudaSuccess ? NSDF_OK : NSDF_ERR_CUDA;
   }

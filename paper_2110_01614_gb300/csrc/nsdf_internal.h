@@ -124,8 +124,10 @@ int query_tc16_min_grid();   // CTAs of one cluster: the smallest grid of the ke
 // 16-bit tensor-core form of the Fourier-feature ReLU networks of Sec. 4.3
 // (width 256, m = 128, 1..8 layers; query_tc16_ff.cu).  Its 16-bit weight
 // copies hold all n_hidden layers, layer l at [l][256][256], layer 0 with the
-// feature columns permuted (ff_feature_of_column).  It needs no scratch.
+// feature columns permuted (ff_feature_of_column).  Its scratch holds the
+// ReLU slope bits, one 28 KB slab per CTA.
 bool query_tc16_ff_supported(int width, int n_hidden, int ff, int relu);
+size_t query_tc16_ff_scratch_bytes(int grid);
 bool make_tc16_ff_tmaps(NetDevice &net, int n_hidden, bool fp16);
 int query_tc16_ff_grid(int64_t n, int num_sms);
 cudaError_t launch_query_tc16_ff(const QueryParams &p, const NetDevice &net, bool fp16,

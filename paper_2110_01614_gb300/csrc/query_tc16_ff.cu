@@ -11,13 +11,13 @@
 //   * every layer z_l = W_l x_l (Eq. 1; layer 0 reads gamma(p)) is 16
 //     tcgen05.mma (M=128, N=256, K=16; 16-bit x 16-bit -> FP32) into TMEM,
 //     A = the 128 x 256 activation tile in shared memory (128-byte swizzled
-//     K-major), B = 256 x 64 weight panels streamed by TMA through a 3-stage
+//     K-major), B = 256 x 64 weight panels streamed by TMA through a 4-stage
 //     ring, each panel fetched half by each CTA of a 2-CTA cluster and
 //     multicast into both,
 //   * the epilogue warps read z from TMEM (tcgen05.ld), add the bias, write
 //     max(z, 0) back over A and keep the ReLU's slope, [z > 0], as one bit
-//     per unit in shared memory (4 KB per layer): the reverse chain needs no
-//     scratch in global memory,
+//     per unit (4 KB per layer and tile, in a per-CTA slab that stays in L2;
+//     shared memory goes to the weight ring),
 //   * the last hidden layer's epilogue forms f = w_out . h in FP32 and starts
 //     the reverse chain with delta = [z > 0] * w_out,
 //   * the Jacobian-transpose chain of Sec. 3.2, g_{l-1} = W_l^T delta_l, runs
@@ -61,14 +61,24 @@ constexpr int kM = 128;                    // points per tile (MMA M, TMEM lanes
 constexpr int kN = 256;                    // MMA N: a whole layer
 constexpr int kKAtom = 64;                 // K elements per 128-byte swizzle atom
 constexpr int kAtoms = kW / kKAtom;        // 4 weight panels per product
-constexpr int kStages = 3;
+// Weight-panel ring depth.  The panels stream from L2 with a latency of about
+// 1.4 us, so the bytes in flight, not the tensor pipe, set the pace of a
+// product: the ring takes all the shared memory the activation tile and the
+// small FP32 weights leave (the ReLU bits live in a per-CTA slab in global
+// memory for that reason).
+constexpr int kStages = 4;
 constexpr int kMaxHidden = 8;
 constexpr int kCluster = 2;
 constexpr int kSliceRows = kN / kCluster;
 constexpr int kStageBytes = kN * kKAtom * 2;     // 32 KB weight panel
 constexpr int kABytes = kM * kW * 2;             // 64 KB activation tile
 constexpr int kAtomBytes = kM * kKAtom * 2;      // 16 KB: one K atom of A
-constexpr int kEpiWarps = 8;
+// Epilogue threads per TMEM lane: each takes kGroupCols columns of every K atom.
+constexpr int kColGroups = 4;
+constexpr int kGroupCols = kKAtom / kColGroups;  // 16
+constexpr int kEpiWarps = 4 * kColGroups;
+// ReLU slope bits of one CTA's tile: 64 bits per row, group and layer
+constexpr int kMaskSlabWords = (kMaxHidden - 1) * kColGroups * kM;   // uint2 entries
 constexpr int kEpiWarp0 = 4;
 constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
 constexpr float kPi = 3.14159265358979324f;
@@ -76,12 +86,11 @@ constexpr float kPi = 3.14159265358979324f;
 // shared-memory map (bytes from a 1024-aligned base)
 constexpr int kOffA = 0;
 constexpr int kOffB = kOffA + kABytes;
-constexpr int kOffMask = kOffB + kStages * kStageBytes;          // uint4 [kMaxHidden-1][2][kM]
-constexpr int kOffBias = kOffMask + (kMaxHidden - 1) * 2 * kM * 16;   // float [kMaxHidden][kW]
+constexpr int kOffBias = kOffB + kStages * kStageBytes;          // float [kMaxHidden][kW]
 constexpr int kOffFreq = kOffBias + kMaxHidden * kW * 4;         // float4 [kFreq]: 2 b_j
 constexpr int kOffWout = kOffFreq + kFreq * 16;                  // float [kW]
-constexpr int kOffExch = kOffWout + kW * 4;                      // float4 [kM]
-constexpr int kOffBar = kOffExch + kM * 16;
+constexpr int kOffExch = kOffWout + kW * 4;                      // float4 [kColGroups-1][kM]
+constexpr int kOffBar = kOffExch + (kColGroups - 1) * kM * 16;
 // barriers: full[kStages], empty[kStages], a_ready[kAtoms], d_full, mma_done, x_full, x_empty
 constexpr int kNumBars = 2 * kStages + kAtoms + 4;
 constexpr int kTmemCols = 2 * kN;                 // two products in flight
@@ -108,24 +117,25 @@ __device__ __forceinline__ void epi_arrive(uint32_t bar, int lane) {
 // Per-thread state of an epilogue thread for one tile.
 struct Epi {
   uint8_t *A;
-  uint4 *mask;          // ReLU slope bits, [layer][column group][row]
+  uint2 *mask;          // this CTA's ReLU slope bits (global), [layer][column group][row]:
+                        // atoms 0, 1 in .x, atoms 2, 3 in .y
   uint32_t t_row;       // TMEM address of lane 32*q, column 0
   uint32_t a_ready;     // barrier a_ready[0]; a_ready[k] is 8 k bytes on
-  int r, ch, lane;      // tile row (= TMEM lane); column group (32 of every atom)
+  int r, ch, lane;      // tile row (= TMEM lane); column group (kGroupCols of every atom)
   float px, py, pz;     // query point in the body frame
-  __device__ __forceinline__ uint4 &bits(int l) const { return mask[(l * 2 + ch) * kM + r]; }
+  __device__ __forceinline__ uint2 &bits(int l) const { return mask[(l * kColGroups + ch) * kM + r]; }
 };
 
-// One 32-column chunk of a forward epilogue: z = D + b, h = max(z, 0); the
-// 16 packed words of the next A operand go to `w` and the slope bits are
-// returned.  The last layer adds w_out . h to fpart and writes
-// delta = [z > 0] * w_out instead of h.
+// One chunk (kGroupCols columns) of a forward epilogue: z = D + b,
+// h = max(z, 0); the packed words of the next A operand go to `w` and the
+// slope bits are returned.  The last layer adds w_out . h to fpart and
+// writes delta = [z > 0] * w_out instead of h.
 template <bool kF16, bool LAST>
-__device__ __forceinline__ uint32_t fwd_chunk(int l, int c0, const uint32_t (&raw)[32], float &fpart,
-                                              uint32_t (&w)[16]) {
+__device__ __forceinline__ uint32_t fwd_chunk(int l, int c0, const uint32_t (&raw)[kGroupCols],
+                                              float &fpart, uint32_t (&w)[kGroupCols / 2]) {
   uint32_t bits = 0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < kGroupCols / 4; ++q) {
     const float4 b = lds4(kOffBias, (l * kW + c0) / 4 + q);
     float4 wo = make_float4(0.f, 0.f, 0.f, 0.f);
     if (LAST) wo = lds4(kOffWout, c0 / 4 + q);
@@ -151,80 +161,81 @@ __device__ __forceinline__ uint32_t fwd_chunk(int l, int c0, const uint32_t (&ra
   return bits;
 }
 
-// One 32-column chunk of a reverse epilogue: delta = [z > 0] * g.
+// One chunk of a reverse epilogue: delta = [z > 0] * g.
 template <bool kF16>
-__device__ __forceinline__ void bwd_chunk(uint32_t bits, const uint32_t (&raw)[32], uint32_t (&w)[16]) {
+__device__ __forceinline__ void bwd_chunk(uint32_t bits, const uint32_t (&raw)[kGroupCols],
+                                          uint32_t (&w)[kGroupCols / 2]) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
+  for (int q = 0; q < kGroupCols / 2; ++q) {
     const float g0 = ((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[2 * q]) : 0.0f;
     const float g1 = ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[2 * q + 1]) : 0.0f;
     w[q] = pack16<kF16>(g0, g1);
   }
 }
 
-// Columns of chunk k (0..3) of this thread: 32 columns of K atom k.  Both
-// column groups work through the atoms in order, so atom k of the next A
-// operand is complete, and announced on a_ready[k], after a quarter of the
+// Columns of chunk k (0..3) of this thread: kGroupCols columns of K atom k.
+// All column groups work through the atoms in order, so atom k of the next
+// A operand is complete, and announced on a_ready[k], after a quarter of the
 // epilogue, and the next product starts on it while the rest is written.
-__device__ __forceinline__ int chunk_col(const Epi &e, int k) { return 64 * k + 32 * e.ch; }
+__device__ __forceinline__ int chunk_col(const Epi &e, int k) { return kKAtom * k + kGroupCols * e.ch; }
 
 // Forward epilogue of layer l, product in TMEM columns dcol..dcol+255 (the
 // next chunk's TMEM load is issued while the current one is processed).
 template <bool kF16, bool LAST>
 __device__ __forceinline__ void fwd_product(const Epi &e, int l, uint32_t dcol, float &fpart) {
   const uint32_t t = e.t_row + dcol;
-  uint32_t ra[32], rb[32], bits[4], w[16];
-  tmem_ld32_async(t + chunk_col(e, 0), ra);
+  uint32_t ra[kGroupCols], rb[kGroupCols], bits[4], w[kGroupCols / 2];
+  tmem_ld16_async(t + chunk_col(e, 0), ra);
 #pragma unroll
   for (int k = 0; k < 4; k += 2) {
     tmem_wait_ld(ra);
-    tmem_ld32_async(t + chunk_col(e, k + 1), rb);
+    tmem_ld16_async(t + chunk_col(e, k + 1), rb);
     bits[k] = fwd_chunk<kF16, LAST>(l, chunk_col(e, k), ra, fpart, w);
-    store_a_chunk(e.A, e.r, chunk_col(e, k), w);
+    store_a_cols(e.A, e.r, chunk_col(e, k), w);
     epi_arrive(e.a_ready + 8u * k, e.lane);
     tmem_wait_ld(rb);
-    if (k + 2 < 4) tmem_ld32_async(t + chunk_col(e, k + 2), ra);
+    if (k + 2 < 4) tmem_ld16_async(t + chunk_col(e, k + 2), ra);
     bits[k + 1] = fwd_chunk<kF16, LAST>(l, chunk_col(e, k + 1), rb, fpart, w);
-    store_a_chunk(e.A, e.r, chunk_col(e, k + 1), w);
+    store_a_cols(e.A, e.r, chunk_col(e, k + 1), w);
     epi_arrive(e.a_ready + 8u * (k + 1), e.lane);
   }
-  if (!LAST) e.bits(l) = make_uint4(bits[0], bits[1], bits[2], bits[3]);
+  if (!LAST) e.bits(l) = make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16));
 }
 
-// Reverse epilogue of layer l >= 1: delta_{l-1} = [z_{l-1} > 0] * g_{l-1}.
+// Reverse epilogue of layer l >= 1: delta_{l-1} = [z_{l-1} > 0] * g_{l-1};
+// m = the slope bits of layer l-1 (loaded before the product was awaited).
 template <bool kF16>
-__device__ __forceinline__ void bwd_product(const Epi &e, int l, uint32_t dcol) {
+__device__ __forceinline__ void bwd_product(const Epi &e, uint2 m, uint32_t dcol) {
   const uint32_t t = e.t_row + dcol;
-  const uint4 m = e.bits(l - 1);
-  const uint32_t bits[4] = {m.x, m.y, m.z, m.w};
-  uint32_t ra[32], rb[32], w[16];
-  tmem_ld32_async(t + chunk_col(e, 0), ra);
+  const uint32_t bits[4] = {m.x & 0xFFFFu, m.x >> 16, m.y & 0xFFFFu, m.y >> 16};
+  uint32_t ra[kGroupCols], rb[kGroupCols], w[kGroupCols / 2];
+  tmem_ld16_async(t + chunk_col(e, 0), ra);
 #pragma unroll
   for (int k = 0; k < 4; k += 2) {
     tmem_wait_ld(ra);
-    tmem_ld32_async(t + chunk_col(e, k + 1), rb);
+    tmem_ld16_async(t + chunk_col(e, k + 1), rb);
     bwd_chunk<kF16>(bits[k], ra, w);
-    store_a_chunk(e.A, e.r, chunk_col(e, k), w);
+    store_a_cols(e.A, e.r, chunk_col(e, k), w);
     epi_arrive(e.a_ready + 8u * k, e.lane);
     tmem_wait_ld(rb);
-    if (k + 2 < 4) tmem_ld32_async(t + chunk_col(e, k + 2), ra);
+    if (k + 2 < 4) tmem_ld16_async(t + chunk_col(e, k + 2), ra);
     bwd_chunk<kF16>(bits[k + 1], rb, w);
-    store_a_chunk(e.A, e.r, chunk_col(e, k + 1), w);
+    store_a_cols(e.A, e.r, chunk_col(e, k + 1), w);
     epi_arrive(e.a_ready + 8u * (k + 1), e.lane);
   }
 }
 
-// gamma(p) for the thread's 64 frequencies j = 64 blk + 32 ch + i: in the
-// permuted column order their sines are chunk 2 blk and their cosines chunk
-// 2 blk + 1 of this thread.
+// gamma(p) for the thread's 2 x kGroupCols frequencies
+// j = 64 blk + kGroupCols ch + i: in the permuted column order their sines
+// are chunk 2 blk and their cosines chunk 2 blk + 1 of this thread.
 template <bool kF16>
 __device__ __forceinline__ void feature_stage(const Epi &e) {
 #pragma unroll 1
   for (int blk = 0; blk < 2; ++blk) {
-    uint32_t sw[16], cw[16];
+    uint32_t sw[kGroupCols / 2], cw[kGroupCols / 2];
 #pragma unroll
-    for (int i = 0; i < 32; i += 2) {
-      const int j = 64 * blk + 32 * e.ch + i;
+    for (int i = 0; i < kGroupCols; i += 2) {
+      const int j = 64 * blk + kGroupCols * e.ch + i;
       const float4 b0 = lds4(kOffFreq, j), b1 = lds4(kOffFreq, j + 1);
       float s0, c0, s1, c1;
       ff_sincos16(b0.x, b0.y, b0.z, e.px, e.py, e.pz, s0, c0);
@@ -232,9 +243,9 @@ __device__ __forceinline__ void feature_stage(const Epi &e) {
       sw[i / 2] = pack16<kF16>(s0, s1);
       cw[i / 2] = pack16<kF16>(c0, c1);
     }
-    store_a_chunk(e.A, e.r, chunk_col(e, 2 * blk), sw);
+    store_a_cols(e.A, e.r, chunk_col(e, 2 * blk), sw);
     epi_arrive(e.a_ready + 16u * blk, e.lane);
-    store_a_chunk(e.A, e.r, chunk_col(e, 2 * blk + 1), cw);
+    store_a_cols(e.A, e.r, chunk_col(e, 2 * blk + 1), cw);
     epi_arrive(e.a_ready + 16u * blk + 8u, e.lane);
   }
 }
@@ -247,14 +258,14 @@ __device__ __forceinline__ void feature_jacobian(const Epi &e, uint32_t dcol, fl
   const uint32_t t = e.t_row + dcol;
 #pragma unroll 1
   for (int blk = 0; blk < 2; ++blk) {
-    uint32_t us[32], uc[32];
-    tmem_ld32_async(t + chunk_col(e, 2 * blk), us);
-    tmem_ld32_async(t + chunk_col(e, 2 * blk + 1), uc);
+    uint32_t us[kGroupCols], uc[kGroupCols];
+    tmem_ld16_async(t + chunk_col(e, 2 * blk), us);
+    tmem_ld16_async(t + chunk_col(e, 2 * blk + 1), uc);
     tmem_wait_ld(us);
     tmem_wait_ld(uc);   // ties uc's registers to the (already complete) wait
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const int j = 64 * blk + 32 * e.ch + i;
+    for (int i = 0; i < kGroupCols; ++i) {
+      const int j = 64 * blk + kGroupCols * e.ch + i;
       const float4 b = lds4(kOffFreq, j);
       float sn, cs;
       ff_sincos16(b.x, b.y, b.z, e.px, e.py, e.pz, sn, cs);
@@ -304,8 +315,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int k = 0; k < kAtoms; ++k) mbar_init(a_ready + 8u * k, kEpiWarps);
     mbar_init(d_full, 1);
     mbar_init(mma_done, 1);
-    mbar_init(x_full, kEpiWarps / 2);
-    mbar_init(x_empty, kEpiWarps / 2);
+    mbar_init(x_full, kEpiWarps - 4);   // the warps of column groups 1..
+    mbar_init(x_empty, 4);              // the warps of column group 0
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     fence_proxy_async();
@@ -423,11 +434,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= kEpiWarp0) {
     // ---------------- epilogue warps ----------------
     const int q = warp & 3;                  // TMEM lane quarter
-    const int ch = (warp - kEpiWarp0) >> 2;  // columns 0..127 or 128..255
+    const int ch = (warp - kEpiWarp0) >> 2;  // column group
     const int r = 32 * q + lane;             // row of the tile = TMEM lane
     Epi e;
     e.A = smem + kOffA;
-    e.mask = reinterpret_cast<uint4 *>(smem + kOffMask);
+    e.mask = reinterpret_cast<uint2 *>(prm.scratch) + (size_t)blockIdx.x * kMaskSlabWords;
     e.t_row = tmem + ((uint32_t)(32 * q) << 16);
     e.a_ready = a_ready;
     e.r = r;
@@ -470,8 +481,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // ---- Jacobian-transpose chain: layers L-1 .. 1, product 2L-1-l ----
       for (int l = L - 1; ok && l >= 1; --l) {
+        const uint2 m = e.bits(l - 1);    // in flight while the product is awaited
         if (!wait_product()) { fail(); ok = false; break; }
-        bwd_product<kF16>(e, l, dcol(G - 1 - l));
+        bwd_product<kF16>(e, m, dcol(G - 1 - l));
       }
       if (!ok) break;
       // ---- layer 0 (product 2L-1): g_gamma through the feature Jacobian ----
@@ -480,10 +492,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       gx *= kPi; gy *= kPi; gz *= kPi;
 
-      // ---- combine the two column halves, normalise, test, project ----
-      if (ch == 1) {
+      // ---- combine the column groups, normalise, test, project ----
+      if (ch != 0) {
         if (!mbar_wait(x_empty, x_phase ^ 1u, budget, abort_flag)) { fail(); ok = false; break; }
-        exch[r] = make_float4(gx, gy, gz, fpart);
+        exch[(ch - 1) * kM + r] = make_float4(gx, gy, gz, fpart);
         __syncwarp();
         if (lane == 0) mbar_arrive(x_full);
         x_phase ^= 1u;
@@ -491,12 +503,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!mbar_wait(x_full, x_phase, budget, abort_flag)) { fail(); ok = false; break; }
       x_phase ^= 1u;
-      const float4 o = exch[r];
+#pragma unroll
+      for (int g = 0; g < kColGroups - 1; ++g) {
+        const float4 o = exch[g * kM + r];
+        gx += o.x; gy += o.y; gz += o.z; fpart += o.w;
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(x_empty);
       if (idx < prm.n) {
-        gx += o.x; gy += o.y; gz += o.z;
-        const float f = fpart + o.w + __ldg(prm.bout);
+        const float f = fpart + __ldg(prm.bout);
         const float nrm = sqrtf(gx * gx + gy * gy + gz * gz);
         float nx = 0.f, ny = 0.f, nz = 0.f;
         if (nrm >= 1e-20f) { nx = gx / nrm; ny = gy / nrm; nz = gz / nrm; }
@@ -620,6 +635,8 @@ cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cu
 bool query_tc16_ff_supported(int width, int n_hidden, int ff, int relu) {
   return width == kW && ff == kFreq && relu != 0 && n_hidden >= 1 && n_hidden <= kMaxHidden;
 }
+
+size_t query_tc16_ff_scratch_bytes(int grid) { return (size_t)grid * kMaskSlabWords * sizeof(uint2); }
 
 bool make_tc16_ff_tmaps(NetDevice &net, int n_hidden, bool fp16) {
   if (n_hidden < 1 || n_hidden > kMaxHidden) return false;

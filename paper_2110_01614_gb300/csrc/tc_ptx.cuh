@@ -144,6 +144,41 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
                : "memory");
 }
 
+// The same for 16 columns.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
+// Store 16-bit values (W / 2 packed words) of row r, columns k0..k0+W-1
+// (W = 16 or 32, k0 a multiple of 8 within one atom), into a 128-row K-major
+// tile in the 128-byte swizzle layout (64-column atoms of 16 KB; 16-byte
+// chunk j of a row sits at chunk j ^ (r % 8)).
+template <int NW>
+__device__ __forceinline__ void store_a_cols(uint8_t *A, int r, int k0, const uint32_t (&w)[NW]) {
+  const int atom = k0 >> 6;
+  const int j0 = (k0 & 63) >> 3;
+  uint8_t *row = A + atom * 16384 + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+  for (int t = 0; t < NW / 4; ++t) {
+    const int phys = (j0 + t) ^ (r & 7);
+    *reinterpret_cast<uint4 *>(row + phys * 16) = make_uint4(w[4 * t], w[4 * t + 1], w[4 * t + 2], w[4 * t + 3]);
+  }
+}
+
 // Store 32 16-bit values (16 packed words) of row r, columns k0..k0+31, into
 // a 128-row K-major tile in the 128-byte swizzle layout (64-column atoms of
 // 16 KB; 16-byte chunk j of a row sits at chunk j ^ (r % 8)).
