@@ -311,6 +311,19 @@ def run_gpu(args):
                        "ns": out_ns.cpu().numpy(), "hit": out_hit.cpu().numpy().astype(bool)}
         ctx.close()
 
+    # --- the paper's own network shapes (Sec. 4.3) on the same points, BF16 tensor cores ---
+    paper = {}
+    if "paper" in forms:
+        for name, L in (("dragon_8x256", 8), ("bunny_4x256", 4)):
+            arch = synth.Arch(3, 256, L, -1, 100.0, "relu", 128)
+            ctx = nsdf.NeuralSDF(arch, nsdf.NSDF_BF16).load(synth.fourier_relu_init(arch, 0))
+            d = timed_steps(ctx, max(2, min(args.steps, 5)), 1)
+            ctx.close()
+            t = statistics.mean(d)
+            flop = 2 * (2 * L * 256 * 256 + 256) * n
+            paper[name] = {"value": n / t, "unit": "queries/s", "ms_per_step": 1e3 * t,
+                           "tflops": flop / t / 1e12, "kernel": "query_tc16_ff_kernel<bf16>"}
+
     # --- end to end through the C ABI with host (pinned) buffers ---
     e2e_value = None
     if not args.no_e2e:
@@ -355,6 +368,13 @@ def run_gpu(args):
                   for name, o in other.items()},
         "clocks": clk,
     }
+    if paper:
+        peak_note = f"{peak_kind} bf16_tflops"
+        for o in paper.values():
+            o["frac_of_peak"] = o["tflops"] / peak_tf
+        line["paper_networks"] = {"workload": "the paper's Fourier-feature ReLU shapes (128 "
+                                              "frequencies, 8 or 4 layers of 256), same points",
+                                  "peak": peak_note, **paper}
     if rank == 0:
         errs = {"bf16": error_stats(bf_ns[sample_idx], bf_hit[sample_idx], pts_h[sample_idx], blob)}
         for name, o in other.items():
@@ -383,7 +403,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # profiling conveniences (the defaults are the benchmark)
     ap.add_argument("--points", type=int, default=N_POINTS)
-    ap.add_argument("--forms", default="bf16,fp16,fp32")
+    ap.add_argument("--forms", default="bf16,fp16,fp32,paper")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -191,3 +191,25 @@ def test_empty_input(nsdf):
     s.collide(d, EPS, out_pts=torch.empty_like(d))
     nsdf.nsdf_sync_status(s.ctx)
     s.close()
+
+
+def test_bounded_wait_reports_timeout_and_recovers(nsdf):
+    """A dropped weight load makes the MMA warp's wait run out: the kernel must
+    return, the context must report NSDF_ERR_TIMEOUT, and the next call must
+    succeed with correct results."""
+    blob = synth.fourier_relu_init(BUNNY, 11)
+    pts = synth.body_scale_points(300, 12)
+    s = nsdf.NeuralSDF(BUNNY, nsdf.NSDF_BF16).load(blob)
+    d = torch.from_numpy(pts).cuda()
+    nsdf.nsdf_debug_inject(s.ctx, 0, 20_000_000)
+    s.collide(d, EPS)
+    with pytest.raises(nsdf.NsdfError) as e:
+        nsdf.nsdf_sync_status(s.ctx)
+    assert e.value.status == 7
+    nsdf.nsdf_debug_inject(s.ctx, -1, 4_000_000_000)
+    out_ns = torch.empty_like(d)
+    s.collide(d, EPS, out_n_sdf=out_ns)
+    nsdf.nsdf_sync_status(s.ctx)
+    s.close()
+    f_r, _, _ = rounded.query_ff_relu(blob, BUNNY, pts[:, :3].astype(np.float64), "bf16")
+    assert np.abs(out_ns.cpu().numpy()[:, 3] - f_r).max() <= 8 * U["bf16"]
