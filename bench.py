@@ -43,11 +43,12 @@ FLOP_PER_QUERY = 2 * MAC_PER_QUERY
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the tensor-core kernel on this workload, from one ncu capture, keyed by the
-# SHA-256 of the kernel source's code (comments and blank lines removed) it was
-# taken on; reported only while that code is unchanged.
+# SHA-256 of the kernel's code (query_tc16.cu and its inline-PTX header
+# tc_ptx.cuh, comments and blank lines removed) it was taken on; reported
+# only while that code is unchanged.
 TRAFFIC_CAPTURE = {
-    "code_sha256": "6f239a4a737f9a6ec9acc3bca1e8fc8e41b2d4bc646091ec4aa5d97d4701c722",
-    "bytes_per_launch": 3.939950e9 + 4.830467e9,
+    "code_sha256": "d225177155c67410c949b30ae8bde4a16a80ea308e6cb760cec0fde145f5efcd",
+    "bytes_per_launch": 3.992628e9 + 4.863712e9,
 }
 
 
@@ -63,11 +64,20 @@ def code_sha256(text):
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
+KERNEL_SOURCES = ("query_tc16.cu", "tc_ptx.cuh")
+
+
+def kernel_code_sha256():
+    text = []
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2110_01614_gb300", "csrc", name)) as f:
+            text.append(f.read())
+    return code_sha256("\n".join(text))
+
+
 def traffic_bytes():
-    src = os.path.join(ROOT, "paper_2110_01614_gb300", "csrc", "query_tc16.cu")
     try:
-        with open(src) as f:
-            h = code_sha256(f.read())
+        h = kernel_code_sha256()
     except OSError:
         return None
     return TRAFFIC_CAPTURE["bytes_per_launch"] if h == TRAFFIC_CAPTURE["code_sha256"] else None

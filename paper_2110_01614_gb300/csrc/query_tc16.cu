@@ -49,9 +49,12 @@
 #include <cudaTypedefs.h>
 
 #include "nsdf_internal.h"
+#include "tc_ptx.cuh"
 
 namespace nsdf {
 namespace {
+
+using namespace ptx;
 
 constexpr int kW = 512;                    // network width handled here
 constexpr int kM = 128;                    // points per tile (MMA M, TMEM lanes)
@@ -118,24 +121,12 @@ constexpr int kOffExch = ((kOffAbort + 4 + 15) / 16) * 16;   // float4 [kM]
 constexpr int kSmemBytes = kOffExch + kM * 16;
 static_assert(kSmemBytes <= 232448, "shared memory budget");
 
-// Instruction descriptor of tcgen05.mma .kind::f16: D F32 (bits 4-5 = 1),
-// A and B of the same 16-bit format, both K-major, N >> 3 at bits 17-22,
-// M >> 4 at bits 24-28.
-// Operand format code (bits 7-9 and 10-12): 0 = F16, 1 = BF16.
+// Operand format of the 16-bit products (FP16 or BF16), and the unpacking of
+// a packed pair.
 template <bool kF16>
 struct Op {
-  static constexpr uint32_t fmt = kF16 ? 0u : 1u;
-  static constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) |
-                                    ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
-  static __device__ __forceinline__ uint32_t pack(float lo, float hi) {
-    if constexpr (kF16) {
-      __half2 t = __floats2half2_rn(lo, hi);
-      return *reinterpret_cast<uint32_t *>(&t);
-    } else {
-      __nv_bfloat162 t = __floats2bfloat162_rn(lo, hi);
-      return *reinterpret_cast<uint32_t *>(&t);
-    }
-  }
+  static constexpr uint32_t idesc = idesc_f16(kF16, kM, kN);
+  static __device__ __forceinline__ uint32_t pack(float lo, float hi) { return pack16<kF16>(lo, hi); }
   static __device__ __forceinline__ float2 unpack(uint32_t u) {
     if constexpr (kF16) {
       __half2 t = *reinterpret_cast<__half2 *>(&u);
@@ -146,144 +137,6 @@ struct Op {
     }
   }
 };
-
-// Shared-memory matrix descriptor for a K-major operand in the 128-byte
-// swizzle layout: 8-row groups 1024 bytes apart (SBO), descriptor version 1
-// (bits 46-47), layout type 2 = SWIZZLE_128B (bits 61-63).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity.  Gives up (false) when
-// the budget of clock cycles is spent or another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget,
-                                       volatile int *abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > budget) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-// Load a box into the same shared-memory offset of every CTA in `mask`,
-// completing the transaction bytes on each CTA's barrier at offset `bar`.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                               uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;\n" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
-      : "memory");
-}
-// Arrive on the barrier at offset `bar` of every CTA in `mask` once this
-// thread's previously issued MMAs have completed.
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;\n" ::"r"(bar), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void mma_16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                       uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
-      : "memory");
-}
-
-// Issue a load of 32 consecutive FP32 columns of this thread's TMEM lane; the
-// registers are valid only after tmem_wait_ld() on the same array.
-__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-// Wait for every outstanding TMEM load of this thread.  The registers of `r`
-// are tied to the wait so the compiler cannot read them before it.
-__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
-                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
-                 "+r"(r[30]), "+r"(r[31])
-               :
-               : "memory");
-}
-
-// Store 32 16-bit values (16 packed words) of row r, columns k0..k0+31, into
-// the 128-byte-swizzled K-major activation tile.
-__device__ __forceinline__ void store_a_chunk(uint8_t *A, int r, int k0, const uint32_t (&w)[16]) {
-  const int atom = k0 >> 6;
-  const int j0 = (k0 & 63) >> 3;
-  uint8_t *row = A + atom * kAtomBytes + (r >> 3) * 1024 + (r & 7) * 128;
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int phys = (j0 + t) ^ (r & 7);
-    uint4 v = make_uint4(w[4 * t], w[4 * t + 1], w[4 * t + 2], w[4 * t + 3]);
-    *reinterpret_cast<uint4 *>(row + phys * 16) = v;
-  }
-}
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -931,7 +784,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t b_stage = sB + stage * kStageBytes;
 #pragma unroll
             for (int ks = 0; ks < kKAtom / 16; ++ks) {
-              mma_16(d, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32),
+              mma_f16(d, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32),
                      Op<kF16>::idesc, (pos | ks) != 0 ? 1u : 0u);
             }
             mma_commit_mc(empty_bar(stage), cmask);
@@ -1114,21 +967,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 bool encode_panel_map(CUtensorMap *map, void *base, int rows, bool fp16) {
-  auto fn = encode_fn();
+  auto fn = tensor_map_encoder();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)kW, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kW * 2};

@@ -1,10 +1,14 @@
 // Inline-PTX building blocks of the tcgen05 kernels: mbarriers with bounded
 // waits, 2-D TMA loads multicast within a cluster, tcgen05.mma of kind::f16
 // with its commit, TMEM loads, the 128-byte-swizzle shared-memory descriptor
-// and the matching store of a 128-row K-major activation tile.
+// and the matching stores of a 128-row K-major activation tile, and the
+// host's tensor-map encoder.
 #pragma once
 
 #include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 namespace nsdf {
@@ -203,6 +207,21 @@ __device__ __forceinline__ uint32_t pack16(float lo, float hi) {
     __nv_bfloat162 t = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&t);
   }
+}
+
+// The driver's cuTensorMapEncodeTiled, looked up once through the runtime
+// (host code; null if the driver does not provide it).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
 }
 
 }  // namespace ptx
