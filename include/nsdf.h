@@ -106,8 +106,11 @@ size_t nsdf_num_params(const nsdf_arch *arch);
  * this build handles (arch, prec): FP32 takes widths 32, 64, 128, 256 and
  * 512 with either activation and Fourier features; BF16 and FP16 take
  * softplus networks of width 512 with at least two hidden layers and no
- * Fourier features (a ReLU slope is a 0/1 decision on the sign of z, which
- * 16-bit pre-activations would flip for many points).
+ * Fourier features, and the Fourier-feature ReLU networks of Sec. 4.3 of
+ * width 256 (ff_freqs = 128) with 1 to 8 layers and no skip layer.  In the
+ * 16-bit forms a ReLU slope is decided on the 16-bit network's own
+ * pre-activations: near z = 0 it can differ from an FP32 or exact
+ * evaluation, and with it the normal.
  */
 nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets,
                         nsdf_ctx **out);
@@ -197,8 +200,9 @@ nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n,
  * activations with FP32 accumulation (cuBLAS); the other sums are FP32 and
  * reduced in a fixed order, so repeated calls give identical results.  Uses
  * about 2 n_hidden x width x 2 bytes of device memory per point, allocated on
- * the first call and when n grows.  FP32 contexts: NSDF_ERR_UNSUPPORTED (use
- * nsdf_backward); n = 0: NSDF_ERR_INVALID_ARG.
+ * the first call and when n grows.  FP32 contexts and Fourier-feature ReLU
+ * networks: NSDF_ERR_UNSUPPORTED (use nsdf_backward for FP32 softplus
+ * networks); n = 0: NSDF_ERR_INVALID_ARG.
  */
 nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n,
                          const float *targets, float *g_weights, float *loss,
