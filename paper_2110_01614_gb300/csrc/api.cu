@@ -466,6 +466,15 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
   const int W = arch->width, L = arch->n_hidden;
   ctx->nets.resize(n_nets);
   nsdf_status st = NSDF_OK;
+  // Fourier-feature 16-bit contexts keep every network's 16-bit weights in one
+  // array, network k at k * n_hidden * W * W, so that one tensor map (that of
+  // network 0) reaches all of them in a grouped launch
+  uint16_t *ff16_fwd = nullptr, *ff16_bwd = nullptr;
+  const size_t ff16_per = (size_t)L * W * W;
+  if (prec != NSDF_FP32 && arch->ff_freqs > 0) {
+    st = ctx_alloc(ctx, &ff16_fwd, ff16_per * n_nets);
+    if (st == NSDF_OK) st = ctx_alloc(ctx, &ff16_bwd, ff16_per * n_nets);
+  }
   for (int k = 0; k < n_nets && st == NSDF_OK; ++k) {
     NetDevice &d = ctx->nets[k];
     const size_t hid = (size_t)(L > 1 ? L - 1 : 1) * W * W;
@@ -481,9 +490,13 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
       if (st == NSDF_OK) st = ctx_alloc(ctx, &d.ff0, (size_t)W * W);
     }
     if (st == NSDF_OK && prec != NSDF_FP32) {
-      const size_t n16 = arch->ff_freqs > 0 ? (size_t)L * W * W : hid;   // + layer 0
-      st = ctx_alloc(ctx, &d.fwd16, n16);
-      if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd16, n16);
+      if (arch->ff_freqs > 0) {        // layer 0 included
+        d.fwd16 = ff16_fwd + ff16_per * k;
+        d.bwd16 = ff16_bwd + ff16_per * k;
+      } else {
+        st = ctx_alloc(ctx, &d.fwd16, hid);
+        if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd16, hid);
+      }
     }
   }
   if (st == NSDF_OK) st = ctx_alloc(ctx, &ctx->d_err, 4);
@@ -571,7 +584,7 @@ nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w, size_t n_f
   }
   if (e != cudaSuccess) return map_err(e);
   const bool fp16 = ctx->prec == NSDF_FP16;
-  if (use_tc16_ff(ctx) ? !make_tc16_ff_tmaps(ctx->nets[net], a.n_hidden, fp16)
+  if (use_tc16_ff(ctx) ? !make_tc16_ff_tmaps(ctx->nets[net], a.n_hidden, net == 0 ? ctx->n_nets : 1, fp16)
                        : use_bf16(ctx) && !make_tc16_tmaps(ctx->nets[net], a.width, a.n_hidden, fp16))
     return NSDF_ERR_CUDA;
   ctx->nets[net].loaded = true;
@@ -735,7 +748,41 @@ int grouped_grid(const nsdf_ctx *ctx, int pt, int cps, int64_t max_total) {
   return (int)(max_tiles < cap ? max_tiles : cap);
 }
 
+// Grouped launch of the 16-bit Fourier-feature kernel: 128-point tiles, each
+// network's tile count rounded up to even (a 2-CTA cluster takes two tiles of
+// one network at a time).
+nsdf_status grouped_launch_tc16_ff(nsdf_ctx *ctx, const GroupedArgs &g, cudaStream_t s) {
+  const int64_t max_tiles = (g.max_total + 127) / 128 + 2 * (int64_t)ctx->n_nets;
+  const int grid = query_tc16_ff_grouped_grid(max_tiles, ctx->num_sms);
+  nsdf_status st = ensure_scratch(ctx, query_tc16_ff_scratch_bytes(grid));
+  if (st != NSDF_OK) return st;
+  cudaError_t e = launch_build_tile_list(g.offsets, g.counts, ctx->n_nets, 128, g.max_total,
+                                         ctx->d_tile_start, ctx->d_err, s, 2);
+  if (e != cudaSuccess) return map_err(e);
+  if (g.T) {
+    e = launch_body_transforms(g.T, ctx->n_nets, ctx->d_body, ctx->d_err, s);
+    if (e != cudaSuccess) return map_err(e);
+  }
+  QueryParams p{};
+  fill_net(ctx, 0, p);
+  p.pts = reinterpret_cast<const float4 *>(g.pts);
+  p.n = g.max_total;
+  p.collide = 1;
+  p.eps = g.eps;
+  p.out_pts = reinterpret_cast<float4 *>(g.out_pts);
+  p.out_n_sdf = reinterpret_cast<float4 *>(g.out_n_sdf);
+  p.scratch = ctx->scratch;
+  p.g_nets = ctx->n_nets;
+  p.g_offsets = g.offsets;
+  p.g_counts = g.counts;
+  p.g_tile_start = ctx->d_tile_start;
+  p.g_netptrs = ctx->d_netptrs;
+  p.g_T = g.T ? ctx->d_body : nullptr;
+  return map_err(launch_query_tc16_ff(p, ctx->nets[0], ctx->prec == NSDF_FP16, ctx->num_sms, s));
+}
+
 nsdf_status grouped_launch(nsdf_ctx *ctx, const GroupedArgs &g, int pt, int cps, cudaStream_t s) {
+  if (use_tc16_ff(ctx)) return grouped_launch_tc16_ff(ctx, g, s);
   const nsdf_arch &a = ctx->arch;
   const int grid = grouped_grid(ctx, pt, cps, g.max_total);
   nsdf_status st = ensure_scratch(ctx, fp32_scratch_bytes_pt(a.width, pt, a.n_hidden, grid));
@@ -800,6 +847,15 @@ nsdf_status nsdf_autotune_grouped(nsdf_ctx *ctx, const float *pts, const int64_t
   if (st != NSDF_OK) return st;
   if (max_total == 0) return NSDF_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (use_tc16_ff(ctx)) {   // one shape: a 128-point tile per CTA, one CTA per SM
+    st = grouped_launch(ctx, g, 0, 0, s);
+    if (st == NSDF_OK) st = map_err(cudaStreamSynchronize(s));
+    if (st == NSDF_OK && chosen) {
+      chosen[0] = 0;
+      chosen[1] = 1;
+    }
+    return st;
+  }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return NSDF_ERR_CUDA;

@@ -16,11 +16,14 @@ namespace nsdf {
 namespace {
 
 // One thread builds the prefix sum (at most a few thousand networks).  An
-// entry outside [0, max_total) is dropped (zero tiles) and flagged.
+// entry outside [0, max_total) is dropped (zero tiles) and flagged.  Each
+// network's tile count is rounded up to a multiple of `round_to` (the
+// tensor-core kernel hands tiles to 2-CTA clusters in pairs that must share
+// a network).
 __global__ void build_tile_list_kernel(const int64_t *__restrict__ offsets,
                                        const int64_t *__restrict__ counts, int n_nets, int P,
-                                       int64_t max_total, int32_t *__restrict__ tile_start,
-                                       int *err) {
+                                       int round_to, int64_t max_total,
+                                       int32_t *__restrict__ tile_start, int *err) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   int64_t acc = 0;
   tile_start[0] = 0;
@@ -29,7 +32,7 @@ __global__ void build_tile_list_kernel(const int64_t *__restrict__ offsets,
     int64_t tiles = 0;
     if (c > 0) {
       if (o < 0 || o > max_total - c) atomicExch(err, kDevBadWork);
-      else tiles = (c + P - 1) / P;
+      else tiles = ((c + P - 1) / P + round_to - 1) / round_to * round_to;
     }
     acc += tiles;
     tile_start[k + 1] = (int32_t)acc;
@@ -77,8 +80,9 @@ cudaError_t launch_body_transforms(const float *T, int n_nets, float *out, int *
 
 cudaError_t launch_build_tile_list(const int64_t *offsets, const int64_t *counts, int n_nets, int P,
                                    int64_t max_total, int32_t *tile_start, int *err,
-                                   cudaStream_t s) {
-  build_tile_list_kernel<<<1, 32, 0, s>>>(offsets, counts, n_nets, P, max_total, tile_start, err);
+                                   cudaStream_t s, int round_to) {
+  build_tile_list_kernel<<<1, 32, 0, s>>>(offsets, counts, n_nets, P, round_to, max_total,
+                                          tile_start, err);
   return cudaGetLastError();
 }
 

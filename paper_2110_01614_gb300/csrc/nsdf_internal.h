@@ -128,8 +128,13 @@ int query_tc16_min_grid();   // CTAs of one cluster: the smallest grid of the ke
 // ReLU slope bits, one 28 KB slab per CTA.
 bool query_tc16_ff_supported(int width, int n_hidden, int ff, int relu);
 size_t query_tc16_ff_scratch_bytes(int grid);
-bool make_tc16_ff_tmaps(NetDevice &net, int n_hidden, bool fp16);
+// rows_nets: how many networks' weights follow net's 16-bit copies
+// contiguously (the map of network 0 covers every network of a context, so
+// that a grouped launch addresses network k at rows k * n_hidden * 256)
+bool make_tc16_ff_tmaps(NetDevice &net, int n_hidden, int rows_nets, bool fp16);
 int query_tc16_ff_grid(int64_t n, int num_sms);
+// grouped launches (QueryParams::g_nets > 0): the grid for up to max_tiles tiles
+int query_tc16_ff_grouped_grid(int64_t max_tiles, int num_sms);
 cudaError_t launch_query_tc16_ff(const QueryParams &p, const NetDevice &net, bool fp16,
                                  int num_sms, cudaStream_t s);
 // Column c = 128 g + 64 s + i of that kernel's feature tile holds feature
@@ -155,7 +160,7 @@ void train_state_free(void *state);
 
 cudaError_t launch_build_tile_list(const int64_t *offsets, const int64_t *counts, int n_nets, int P,
                                    int64_t max_total, int32_t *tile_start, int *err,
-                                   cudaStream_t s);
+                                   cudaStream_t s, int round_to = 1);
 // T [n_nets][16] (row-major 4x4 poses, device) -> out [n_nets][kBodyFloats]
 cudaError_t launch_body_transforms(const float *T, int n_nets, float *out, int *err,
                                    cudaStream_t s);

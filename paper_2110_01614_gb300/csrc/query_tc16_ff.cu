@@ -91,8 +91,9 @@ constexpr int kOffFreq = kOffBias + kMaxHidden * kW * 4;         // float4 [kFre
 constexpr int kOffWout = kOffFreq + kFreq * 16;                  // float [kW]
 constexpr int kOffExch = kOffWout + kW * 4;                      // float4 [kColGroups-1][kM]
 constexpr int kOffBar = kOffExch + (kColGroups - 1) * kM * 16;
-// barriers: full[kStages], empty[kStages], a_ready[kAtoms], d_full, mma_done, x_full, x_empty
-constexpr int kNumBars = 2 * kStages + kAtoms + 4;
+// barriers: full[kStages], empty[kStages], a_ready[kAtoms], d_full, mma_done, x_full, x_empty,
+// w_free, w_ready
+constexpr int kNumBars = 2 * kStages + kAtoms + 6;
 constexpr int kTmemCols = 2 * kN;                 // two products in flight
 constexpr int kOffTmemSlot = kOffBar + 8 * kNumBars;
 constexpr int kOffAbort = kOffTmemSlot + 4;
@@ -277,9 +278,30 @@ __device__ __forceinline__ void feature_jacobian(const Epi &e, uint32_t dcol, fl
   }
 }
 
+// Tile t of a launch: its network, the index of its first point and how many
+// points of that network lie from there on (<= 0: the tile is all masked).
+// Grouped launches (g_nets > 0) take network k for the tiles
+// g_tile_start[k] <= t < g_tile_start[k + 1]; past the last tile the lookup
+// lands on a network whose points are exhausted.
+struct TileRef {
+  int net;
+  int64_t first, valid;
+};
+__device__ __forceinline__ TileRef tile_ref(const QueryParams &prm, int64_t t) {
+  if (prm.g_nets <= 0) return TileRef{0, t * kM, prm.n - t * kM};
+  int lo = 0, hi = prm.g_nets;   // the largest k < g_nets with g_tile_start[k] <= t
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prm.g_tile_start[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  const int64_t lt = t - prm.g_tile_start[lo];
+  return TileRef{lo, prm.g_offsets[lo] + lt * kM, prm.g_counts[lo] - lt * kM};
+}
+
 template <bool kF16>
 __global__ void __launch_bounds__(kThreads, 1)
-    query_tc16_ff_kernel(const QueryParams prm, const __grid_constant__ CUtensorMap tmap_fwd,
+    query_tc16_ff_kernel(const __grid_constant__ QueryParams prm, const __grid_constant__ CUtensorMap tmap_fwd,
                          const __grid_constant__ CUtensorMap tmap_bwd) {
   extern __shared__ __align__(1024) uint8_t g_smem_ff[];
   uint8_t *smem = g_smem_ff;
@@ -298,13 +320,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t mma_done = d_full + 8u;
   const uint32_t x_full = mma_done + 8u;    // columns 128..255 have published their partial sums
   const uint32_t x_empty = x_full + 8u;     // columns 0..127 have consumed them
+  // epilogue warps: done with the small weights of the previous network /
+  // the next network's small weights are in shared memory
+  const uint32_t w_free = x_empty + 8u;
+  const uint32_t w_ready = w_free + 8u;
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + kOffTmemSlot);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kOffAbort);
   float4 *exch = reinterpret_cast<float4 *>(smem + kOffExch);
 
   const int L = prm.n_hidden;
   const int G = 2 * L;                         // products per tile
-  const int64_t ntiles = (prm.n + kM - 1) / kM;
+  const int64_t ntiles = prm.g_nets > 0 ? (int64_t)prm.g_tile_start[prm.g_nets] : (prm.n + kM - 1) / kM;
   const long long budget = prm.wait_budget;
 
   if (threadIdx.x == 0) {
@@ -317,22 +343,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(mma_done, 1);
     mbar_init(x_full, kEpiWarps - 4);   // the warps of column groups 1..
     mbar_init(x_empty, 4);              // the warps of column group 0
+    mbar_init(w_free, kEpiWarps);
+    mbar_init(w_ready, kEpiWarps);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     fence_proxy_async();
-  }
-  {
-    // biases, frequencies and w_out, once per CTA
-    float4 *dst = reinterpret_cast<float4 *>(smem + kOffBias);
-    const float4 *bsrc = reinterpret_cast<const float4 *>(prm.bias);
-    for (int i = threadIdx.x; i < L * kW / 4; i += kThreads) dst[i] = __ldg(bsrc + i);
-    dst = reinterpret_cast<float4 *>(smem + kOffFreq);
-    for (int i = threadIdx.x; i < kFreq; i += kThreads)
-      dst[i] = make_float4(2.f * __ldg(prm.ffB + 3 * i), 2.f * __ldg(prm.ffB + 3 * i + 1),
-                           2.f * __ldg(prm.ffB + 3 * i + 2), 0.f);
-    dst = reinterpret_cast<float4 *>(smem + kOffWout);
-    const float4 *wosrc = reinterpret_cast<const float4 *>(prm.wout);
-    for (int i = threadIdx.x; i < kW / 4; i += kThreads) dst[i] = __ldg(wosrc + i);
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -365,10 +380,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t load_idx = 0;
       bool ok = true;
       for (int64_t it = 0; ok && it < iters; ++it) {
+        const int net = tile_ref(prm, blockIdx.x + it * gridDim.x).net;
         for (int g = 0; ok && g < G; ++g) {
           const bool fwd = g < L;
           const int l = fwd ? g : G - 1 - g;            // network layer of this product
           const CUtensorMap *map = fwd ? &tmap_fwd : &tmap_bwd;
+          const int row0 = (net * L + l) * kW;          // the maps cover every network
           for (int k = 0; k < kAtoms; ++k, ++load_idx) {
             if (!mbar_wait(empty_bar(stage), phase ^ 1u, budget, abort_flag)) {
               fail();
@@ -378,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (load_idx != prm.drop_load) {
               mbar_expect_tx(full_bar(stage), kStageBytes);   // both slices land here
               tma_load_2d_mc(sB + stage * kStageBytes + crank * (kSliceRows * kKAtom * 2), map,
-                             k * kKAtom, l * kW + (int)crank * kSliceRows, full_bar(stage), cmask);
+                             k * kKAtom, row0 + (int)crank * kSliceRows, full_bar(stage), cmask);
               issued_mask |= 1u << stage;
               issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
             }
@@ -444,7 +461,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     e.r = r;
     e.ch = ch;
     e.lane = lane;
-    uint32_t d_phase = 0, x_phase = 0;
+    uint32_t d_phase = 0, x_phase = 0, w_phase = 0;
+    int cur_net = -1;
+    float bout = 0.f;
     bool ok = true;
     // warp-uniform, so that no TMEM load below runs with part of a warp
     auto wait_product = [&]() -> bool {
@@ -454,16 +473,56 @@ __global__ void __launch_bounds__(kThreads, 1)
       return got;
     };
     for (int64_t it = 0; ok && it < iters; ++it) {
-      const int64_t tile = blockIdx.x + it * gridDim.x;
-      const int64_t idx = tile * kM + r;
+      const TileRef tr = tile_ref(prm, blockIdx.x + it * gridDim.x);
+      if (tr.net != cur_net) {
+        // this network's biases, frequencies (2 b_j) and w_out into shared
+        // memory, once every epilogue warp is done with the previous ones
+        const bool grouped = prm.g_nets > 0;
+        const float *bias = grouped ? prm.g_netptrs[tr.net].bias : prm.bias;
+        const float *ffB = grouped ? prm.g_netptrs[tr.net].ffB : prm.ffB;
+        const float *wout = grouped ? prm.g_netptrs[tr.net].wout : prm.wout;
+        const float *bo = grouped ? prm.g_netptrs[tr.net].bout : prm.bout;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(w_free);
+        if (!__all_sync(0xffffffffu, mbar_wait(w_free, w_phase, budget, abort_flag))) {
+          fail(); ok = false; break;
+        }
+        const int et = threadIdx.x - 32 * kEpiWarp0;     // 0 .. 32 kEpiWarps - 1
+        float4 *dst = reinterpret_cast<float4 *>(smem + kOffBias);
+        const float4 *bsrc = reinterpret_cast<const float4 *>(bias);
+        for (int i = et; i < L * kW / 4; i += 32 * kEpiWarps) dst[i] = __ldg(bsrc + i);
+        dst = reinterpret_cast<float4 *>(smem + kOffFreq);
+        for (int i = et; i < kFreq; i += 32 * kEpiWarps)
+          dst[i] = make_float4(2.f * __ldg(ffB + 3 * i), 2.f * __ldg(ffB + 3 * i + 1),
+                               2.f * __ldg(ffB + 3 * i + 2), 0.f);
+        dst = reinterpret_cast<float4 *>(smem + kOffWout);
+        const float4 *wosrc = reinterpret_cast<const float4 *>(wout);
+        for (int i = et; i < kW / 4; i += 32 * kEpiWarps) dst[i] = __ldg(wosrc + i);
+        bout = __ldg(bo);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(w_ready);
+        if (!__all_sync(0xffffffffu, mbar_wait(w_ready, w_phase, budget, abort_flag))) {
+          fail(); ok = false; break;
+        }
+        w_phase ^= 1u;
+        cur_net = tr.net;
+      }
+      // this body's rigid pose (Sec. 4.2): T^{-1} rows 0..2 and T[:3,:3]
+      const float *Ti = nullptr, *R = nullptr;
+      if (prm.g_nets > 0) {
+        if (prm.g_T) { Ti = prm.g_T + (size_t)kBodyFloats * tr.net; R = Ti + 12; }
+      } else if (prm.has_T) {
+        Ti = prm.Ti; R = prm.R;
+      }
+      const bool valid = r < tr.valid;
+      const int64_t idx = tr.first + r;
       float4 pw = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (idx < prm.n) pw = prm.pts[idx];
+      if (valid) pw = prm.pts[idx];
       e.px = pw.x; e.py = pw.y; e.pz = pw.z;
-      if (prm.has_T) {
-        const float *t = prm.Ti;
-        e.px = t[0] * pw.x + t[1] * pw.y + t[2] * pw.z + t[3];
-        e.py = t[4] * pw.x + t[5] * pw.y + t[6] * pw.z + t[7];
-        e.pz = t[8] * pw.x + t[9] * pw.y + t[10] * pw.z + t[11];
+      if (Ti) {
+        e.px = Ti[0] * pw.x + Ti[1] * pw.y + Ti[2] * pw.z + Ti[3];
+        e.py = Ti[4] * pw.x + Ti[5] * pw.y + Ti[6] * pw.z + Ti[7];
+        e.pz = Ti[8] * pw.x + Ti[9] * pw.y + Ti[10] * pw.z + Ti[11];
       }
       float fpart = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 
@@ -510,8 +569,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(x_empty);
-      if (idx < prm.n) {
-        const float f = fpart + __ldg(prm.bout);
+      if (valid) {
+        const float f = fpart + bout;
         const float nrm = sqrtf(gx * gx + gy * gy + gz * gz);
         float nx = 0.f, ny = 0.f, nz = 0.f;
         if (nrm >= 1e-20f) { nx = gx / nrm; ny = gy / nrm; nz = gz / nrm; }
@@ -519,8 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (prm.raw_gradient) { nx = gx; ny = gy; nz = gz; }
           prm.out_n_sdf[idx] = make_float4(nx, ny, nz, f);
         } else {
-          if (prm.has_T) {
-            const float *R = prm.R;
+          if (R) {
             const float wx = R[0] * nx + R[1] * ny + R[2] * nz;
             const float wy = R[3] * nx + R[4] * ny + R[5] * nz;
             const float wz = R[6] * nx + R[7] * ny + R[8] * nz;
@@ -599,7 +657,11 @@ cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cu
   cudaError_t e = cudaFuncSetAttribute(query_tc16_ff_kernel<kF16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
-  const int grid = query_tc16_ff_grid(p.n, num_sms);
+  // grouped: p.n = the largest point index + 1; every network may add a
+  // partial tile and a pairing tile
+  const int grid = p.g_nets > 0
+                       ? query_tc16_ff_grouped_grid((p.n + kM - 1) / kM + 2 * (int64_t)p.g_nets, num_sms)
+                       : query_tc16_ff_grid(p.n, num_sms);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
@@ -625,9 +687,9 @@ bool query_tc16_ff_supported(int width, int n_hidden, int ff, int relu) {
 
 size_t query_tc16_ff_scratch_bytes(int grid) { return (size_t)grid * kMaskSlabWords * sizeof(uint2); }
 
-bool make_tc16_ff_tmaps(NetDevice &net, int n_hidden, bool fp16) {
-  if (n_hidden < 1 || n_hidden > kMaxHidden) return false;
-  const int rows = n_hidden * kW;
+bool make_tc16_ff_tmaps(NetDevice &net, int n_hidden, int rows_nets, bool fp16) {
+  if (n_hidden < 1 || n_hidden > kMaxHidden || rows_nets < 1) return false;
+  const int rows = rows_nets * n_hidden * kW;
   return encode_map(&net.tmap_fwd, net.fwd16, rows, fp16) &&
          encode_map(&net.tmap_bwd, net.bwd16, rows, fp16);
 }
@@ -637,6 +699,13 @@ int query_tc16_ff_grid(int64_t n, int num_sms) {
   const int cap = resident_cluster_ctas(num_sms);
   int64_t g = tiles < cap ? tiles : cap;
   g = (g / kCluster) * kCluster;                 // whole clusters
+  return (int)(g < kCluster ? kCluster : g);
+}
+
+int query_tc16_ff_grouped_grid(int64_t max_tiles, int num_sms) {
+  const int cap = resident_cluster_ctas(num_sms);
+  int64_t g = max_tiles < cap ? max_tiles : cap;
+  g = (g / kCluster) * kCluster;
   return (int)(g < kCluster ? kCluster : g);
 }
 

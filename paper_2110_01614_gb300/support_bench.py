@@ -7,6 +7,9 @@
 * grouped: 16 networks of the 3-64-64-64-1 shape with log-uniform counts in
   [2k, 400k] (about 1.2M points) in one grouped launch, autotuned, replayed
   from a CUDA graph; also with a rigid pose per body (nsdf_query_grouped_T).
+* grouped_paper: the same 16-body scene with every body posed and carrying
+  its own network of the paper's dragon shape (Fourier features + 8 ReLU
+  layers of 256), BF16 tensor cores against the FP32 grouped kernel.
 * cloth: 1024 x 1024 cloth, per-step time of Verlet + collision solve for the
   body-scale network in BF16 / FP16 / FP32, and of the exact brute-force mesh
   SDF of every vertex (20,480 triangles) as the plain reference.
@@ -22,7 +25,8 @@
   the BF16 tensor-core path (pool of 1,048,576 points with exact targets,
   batches of 250,000): seconds per step and the time of nsdf_l1_grad alone.
 
-Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped cloth paper_arch fit512]
+Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped grouped_paper cloth
+                                                      paper_arch fit512]
 """
 
 import json
@@ -112,6 +116,38 @@ def bench_grouped(reps=20):
             "ctas_per_sm": cps, "precision": "fp32"}
 
 
+def bench_grouped_paper(reps=10):
+    """16 posed bodies, each with its own network of the paper's dragon shape,
+    counts as in the grouped workload (about 1.2M points), CUDA-graph replay:
+    BF16 tensor cores against the FP32 grouped kernel."""
+    arch = synth.Arch(3, 256, 8, -1, 100.0, "relu", 128)
+    counts = synth.grouped_counts()
+    offs = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    total = int(counts.sum())
+    P = torch.from_numpy(synth.body_scale_points(total, 5)).cuda()
+    O = torch.from_numpy(offs).cuda()
+    C = torch.from_numpy(counts.astype(np.int64)).cuda()
+    Tdev = torch.from_numpy(synth.rigid_transforms(16, seed=77)).cuda()
+    out, ns = torch.empty_like(P), torch.empty_like(P)
+    res = {"workload": "grouped_paper", "nets": 16, "points": total, "shape": "dragon_8x256"}
+    for prec, name, r in ((NSDF_BF16, "bf16", reps), (NSDF_FP32, "fp32", 3)):
+        net = NeuralSDF(arch, prec, n_nets=16)
+        for k in range(16):
+            net.load(synth.fourier_relu_init(arch, k), net=k)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            nsdf_query_grouped_T(net.ctx, P, O, C, total, 0.002, Tdev, out, ns)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            nsdf_query_grouped_T(net.ctx, P, O, C, total, 0.002, Tdev, out, ns)
+        ms = events_ms(g.replay, r)
+        nsdf_sync_status(net.ctx)
+        net.close()
+        res[name] = {"ms": ms, "queries_per_s": total / (ms * 1e-3)}
+    return res
+
+
 def bench_cloth(steps=20):
     res = {"workload": "cloth", "grid": "1024x1024", "steps": steps}
     blob = synth.geometric_init(BODY, 0)
@@ -172,12 +208,13 @@ def bench_fit512(steps=20):
 
 
 def main(argv):
-    which = argv or ["fit", "penalty", "grouped", "cloth", "paper_arch", "fit512"]
+    which = argv or ["fit", "penalty", "grouped", "grouped_paper", "cloth", "paper_arch", "fit512"]
     torch.cuda.set_device(0)
     for w in which:
         t0 = time.perf_counter()
         r = {"fit": bench_fit, "penalty": bench_penalty, "grouped": bench_grouped,
-             "cloth": bench_cloth, "paper_arch": bench_paper_arch, "fit512": bench_fit512}[w]()
+             "grouped_paper": bench_grouped_paper, "cloth": bench_cloth,
+             "paper_arch": bench_paper_arch, "fit512": bench_fit512}[w]()
         r["wall_s"] = time.perf_counter() - t0
         print(json.dumps(r), flush=True)
 

@@ -213,3 +213,117 @@ def test_bounded_wait_reports_timeout_and_recovers(nsdf):
     s.close()
     f_r, _, _ = rounded.query_ff_relu(blob, BUNNY, pts[:, :3].astype(np.float64), "bf16")
     assert np.abs(out_ns.cpu().numpy()[:, 3] - f_r).max() <= 8 * U["bf16"]
+
+
+# ---- many bodies, each with its own network of the paper's shape, in one launch ----
+
+def grouped_ctx(nsdf, fmt, arch, n_nets, seed):
+    s = nsdf.NeuralSDF(arch, P(nsdf, fmt), n_nets=n_nets)
+    blobs = [synth.fourier_relu_init(arch, seed + k) for k in range(n_nets)]
+    for k, b in enumerate(blobs):
+        s.load(b, net=k)
+    return s, blobs
+
+
+def single_network_runs(nsdf, fmt, arch, blobs, offs, counts, pts):
+    """Every body through its own single-network launch of the same kernel."""
+    out, ns = np.zeros_like(pts), np.zeros_like(pts)
+    for k, b in enumerate(blobs):
+        if counts[k] == 0:
+            continue
+        sl = slice(offs[k], offs[k] + counts[k])
+        o, n_, _ = collide_gpu(nsdf, fmt, arch, b, np.ascontiguousarray(pts[sl]))
+        out[sl], ns[sl] = o, n_
+    return out, ns
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_grouped_equals_single_network_launches(nsdf, fmt):
+    """Eight bodies with counts that give empty, one-point, exactly-one-tile,
+    odd and even tile counts: each row is computed exactly as in a launch of
+    its own network, so the results are bitwise equal."""
+    counts = np.array([0, 1, 127, 128, 129, 300, 2000, 5000], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    total = int(counts.sum())
+    pts = synth.body_scale_points(total, 31)
+    s, blobs = grouped_ctx(nsdf, fmt, BUNNY, len(counts), 40)
+    d = torch.from_numpy(pts).cuda()
+    out, ns = torch.full_like(d, -7.0), torch.full_like(d, -7.0)
+    nsdf.nsdf_query_grouped(s.ctx, d, torch.from_numpy(offs).cuda(), torch.from_numpy(counts).cuda(),
+                            total, EPS, out, ns)
+    nsdf.nsdf_sync_status(s.ctx)
+    s.close()
+    ref_out, ref_ns = single_network_runs(nsdf, fmt, BUNNY, blobs, offs, counts, pts)
+    np.testing.assert_array_equal(out.cpu().numpy(), ref_out)
+    np.testing.assert_array_equal(ns.cpu().numpy(), ref_ns)
+
+
+def test_grouped_posed_scene_against_oracles(nsdf):
+    """Five posed bodies of the dragon shape (Sec. 4.2 per body), one of them
+    empty and one of 129 points (a full tile and a single point), against the
+    oracles body by body."""
+    counts = np.array([1500, 0, 2500, 129, 3000], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    total = int(counts.sum())
+    pts = synth.body_scale_points(total, 32)      # the distribution the statistical bounds are set on
+    T = synth.rigid_transforms(len(counts), seed=33)
+    s, blobs = grouped_ctx(nsdf, "bf16", DRAGON, len(counts), 50)
+    d = torch.from_numpy(pts).cuda()
+    out, ns = torch.zeros_like(d), torch.zeros_like(d)
+    nsdf.nsdf_query_grouped_T(s.ctx, d, torch.from_numpy(offs).cuda(), torch.from_numpy(counts).cuda(),
+                              total, EPS, torch.from_numpy(T).cuda(), out, ns)
+    nsdf.nsdf_sync_status(s.ctx)
+    s.close()
+    out, ns = out.cpu().numpy(), ns.cpu().numpy()
+    for k in range(len(counts)):
+        if counts[k] == 0:
+            continue
+        sl = slice(offs[k], offs[k] + counts[k])
+        hit_k = (ns[sl, 3] < EPS).astype(np.uint8)     # the kernel's own decision f < eps
+        if counts[k] >= 1000:                            # enough points for the statistics
+            check("bf16", DRAGON, blobs[k], pts[sl], out[sl], ns[sl], hit_k, T=T[k])
+        else:
+            f_x, _, hit_x, _ = mlp.collide(blobs[k], DRAGON, pts[sl], EPS, T=T[k])
+            assert np.abs(ns[sl, 3] - f_x).max() <= 24 * U["bf16"]
+            far = np.abs(f_x - EPS) > 24 * U["bf16"]
+            np.testing.assert_array_equal(hit_k[far].astype(bool), hit_x[far])
+
+
+def test_grouped_graph_replays_with_new_counts_and_poses(nsdf):
+    """A captured grouped launch replays correctly after the counts, offsets
+    and poses change on the device (the tile list is rebuilt inside the
+    graph)."""
+    s, blobs = grouped_ctx(nsdf, "bf16", BUNNY, 3, 60)
+    max_total = 6000
+    pts = synth.body_scale_points(max_total, 34)
+    Pd = torch.from_numpy(pts).cuda()
+    O = torch.tensor([0, 1000, 3000], dtype=torch.int64, device="cuda")
+    C = torch.tensor([1000, 2000, 3000], dtype=torch.int64, device="cuda")
+    Td = torch.from_numpy(synth.rigid_transforms(3, seed=35)).cuda()
+    out, ns = torch.zeros_like(Pd), torch.zeros_like(Pd)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        nsdf.nsdf_query_grouped_T(s.ctx, Pd, O, C, max_total, EPS, Td, out, ns)   # warm-up (scratch)
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        nsdf.nsdf_query_grouped_T(s.ctx, Pd, O, C, max_total, EPS, Td, out, ns)
+    cases = ((np.array([0, 1000, 3000]), np.array([1000, 2000, 3000]), 36),
+             (np.array([0, 129, 5000]), np.array([129, 0, 1000]), 37))
+    for offs, counts, seed in cases:
+        T = synth.rigid_transforms(3, seed=seed)
+        O.copy_(torch.from_numpy(offs.astype(np.int64)))
+        C.copy_(torch.from_numpy(counts.astype(np.int64)))
+        Td.copy_(torch.from_numpy(T))
+        ns.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        got = ns.cpu().numpy()
+        for k in range(3):
+            if counts[k] == 0:
+                continue
+            sl = slice(offs[k], offs[k] + counts[k])
+            f_r = mlp.collide(blobs[k], BUNNY, pts[sl], EPS, T=T[k])[0]
+            assert np.abs(got[sl, 3] - f_r).max() <= 24 * U["bf16"]
+    nsdf.nsdf_sync_status(s.ctx)
+    s.close()
