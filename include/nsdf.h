@@ -217,8 +217,10 @@ nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n,
  * max_total bounds offsets[k] + counts[k] (a violating entry is skipped and
  * reported by nsdf_sync_status as NSDF_ERR_INVALID_ARG) and sizes the launch.
  * out_n_sdf nullable; points outside every range are left untouched.
- * Arithmetic: FP32 (the FP32 fused kernel; any precision of the context).
- * The first call with a given max_total may allocate scratch: make it before
+ * Arithmetic: FP32 (the FP32 fused kernel) for every context except the
+ * 16-bit Fourier-feature ReLU ones, which run the tensor-core kernel of
+ * their precision with the same results per point as nsdf_collide.  The
+ * first call with a given max_total may allocate scratch: make it before
  * capturing the call into a graph.
  */
 nsdf_status nsdf_query_grouped(nsdf_ctx *ctx, const float *pts,
@@ -249,7 +251,10 @@ nsdf_status nsdf_query_grouped_T(nsdf_ctx *ctx, const float *pts,
  * thread) and every CTAs-per-SM count that fits on this exact problem
  * (3 timed launches each, CUDA events), keeps the fastest in the context for
  * later nsdf_query_grouped calls and writes it to chosen[0] (points per
- * thread) and chosen[1] (CTAs per SM) when chosen is not NULL.  Runs the
+ * thread) and chosen[1] (CTAs per SM) when chosen is not NULL.  16-bit
+ * Fourier-feature contexts have one grouped shape (a 128-point tile per
+ * CTA, one CTA per SM, on tensor cores): the problem runs once and chosen
+ * receives {0, 1}.  Runs the
  * problem several times (outputs are overwritten with correct results) and
  * synchronises `stream`; do not call it during stream capture.
  */
