@@ -244,3 +244,48 @@ def penalty_grad_closed_form(blob, arch, p, eps):
     f, zs, _ = forward(blob, arch, p)
     g = gradient(blob, arch, p, zs)
     return (-2.0 * np.maximum(0.0, eps - f))[:, None] * g
+
+
+def param_gradient(blob, arch, p, a):
+    """Gradient of L = sum_i a_i f(p_i) with respect to every parameter, in
+    blob layout (first order only; with a_i = sign(f_i - d_i) / n it is the
+    gradient of the L1 fitting loss of Sec. 3.1).
+
+    Reverse mode over the forward pass of Eq. 1: delta_l = slope(z_l) * g_l,
+    dL/dW_l = sum_i a_i delta_l(i) x_l(i)^T, dL/db_l = sum_i a_i delta_l(i),
+    g_{l-1} = W_l^T delta_l (split at the skip layer as in ``gradient``); a
+    Fourier-feature layer's frequencies get
+    dL/dB_j = sum_i a_i 2 pi (g_sin,j cos(2 pi b_j.p) - g_cos,j sin(2 pi b_j.p)) p_i.
+    """
+    p = np.asarray(p, dtype=np.float64)[:, :3]
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    layers = _layers(blob, arch)
+    L = arch.n_hidden
+    _, zs, xs = forward(blob, arch, p)
+    h_last = activation(zs[L - 1], arch)
+    w_out = layers[L][0][0]
+    grads = [None] * (L + 1)
+    grads[L] = ((a @ h_last)[None, :], np.array([a.sum()]))
+    g = np.broadcast_to(w_out, h_last.shape)
+    gB = None
+    for l in range(L - 1, -1, -1):
+        W, _ = layers[l]
+        delta = slope(zs[l], arch) * g
+        ad = a[:, None] * delta
+        grads[l] = (ad.T @ xs[l], ad.sum(0))
+        u = delta @ W
+        if l == 0:
+            if arch.ff_freqs > 0:
+                m = arch.ff_freqs
+                _, phase = fourier_features(blob, arch, p)
+                coef = u[:, :m] * np.cos(phase) - u[:, m:] * np.sin(phase)
+                gB = 2.0 * np.pi * ((a[:, None] * coef).T @ p)
+            break
+        if arch.skip_layer > 0 and l == arch.skip_layer:
+            k = W.shape[1] - 3
+            g = u[:, :k] / SQRT2
+        else:
+            g = u
+    parts = [gB.ravel()] if arch.ff_freqs > 0 else []
+    parts += [np.concatenate([gW.ravel(), gb.ravel()]) for gW, gb in grads]
+    return np.concatenate(parts)

@@ -95,3 +95,45 @@ def query_ff_relu(blob, arch, p, fmt):
     g_gamma = delta @ Wr[0]
     coef = g_gamma[:, :m] * np.cos(phase) - g_gamma[:, m:] * np.sin(phase)
     return f, 2.0 * np.pi * (coef @ B), margin
+
+
+def l1_grad_ff_relu(blob, arch, p, a, fmt):
+    """sum_i a_i d f(p_i) / d theta in blob layout, from the 16-bit operands a
+    tensor-core fitting step saves (the rounding points of the module
+    docstring): dL/dW_l = sum_i a_i delta_l(i) x_l(i)^T with x_0 the rounded
+    features, x_l = the rounded h_{l-1} and delta_l the rounded deltas;
+    dL/db_l = sum_i a_i delta_l(i); dL/dw_out = sum_i a_i h_{L-1}(i) with
+    h_{L-1} rounded as it is saved; dL/db_out = sum_i a_i.  The frequencies B
+    are not trained (random Fourier features): their entries are 0.
+    Sums are exact (FP64).
+    """
+    assert arch.activation == "relu" and arch.ff_freqs > 0
+    p = np.asarray(p, dtype=np.float64)[:, :3]
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    layers = unpack(blob, arch, dtype=np.float64)
+    L, m = arch.n_hidden, arch.ff_freqs
+    B = ff_matrix(blob, arch)
+    phase = 2.0 * np.pi * (p @ B.T)
+    x = round16(np.concatenate([np.sin(phase), np.cos(phase)], axis=1), fmt)
+    Wr = [round16(layers[l][0], fmt) for l in range(L)]
+    xs, masks = [], []
+    h = None
+    for l in range(L):
+        xs.append(x)
+        z = x @ Wr[l].T + layers[l][1]
+        masks.append(z > 0.0)
+        h = np.where(masks[-1], z, 0.0)
+        if l < L - 1:
+            x = round16(h, fmt)
+    w_out = layers[L][0][0]
+    grads = [None] * (L + 1)
+    grads[L] = ((a @ round16(h, fmt))[None, :], np.array([a.sum()]))
+    delta = round16(np.where(masks[L - 1], w_out[None, :], 0.0), fmt)
+    for l in range(L - 1, -1, -1):
+        ad = a[:, None] * delta
+        grads[l] = (ad.T @ xs[l], ad.sum(0))
+        if l > 0:
+            delta = round16(np.where(masks[l - 1], delta @ Wr[l], 0.0), fmt)
+    parts = [np.zeros(m * 3)]
+    parts += [np.concatenate([gW.ravel(), gb.ravel()]) for gW, gb in grads]
+    return np.concatenate(parts)

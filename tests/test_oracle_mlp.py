@@ -394,3 +394,45 @@ def test_relu_slope_is_zero_at_the_kink():
     z = np.array([[-1.0, 0.0, 2.0]])
     np.testing.assert_array_equal(mlp.slope(z, RELU), [[0.0, 0.0, 1.0]])
     np.testing.assert_array_equal(mlp.activation(z, RELU), [[0.0, 0.0, 2.0]])
+
+
+@pytest.mark.parametrize("skip", [-1, 2])
+def test_param_gradient_equals_loss_backward_without_tangent(skip):
+    """The first-order parameter gradient is loss_backward with v = 0 (pinned
+    above by central differences), for softplus networks with and without a
+    skip layer."""
+    arch = synth.Arch(3, 16, 4, skip, 100.0)
+    blob = pack(random_layers(arch, 41))
+    p = synth.uniform_cube(40, 42)[:, :3].astype(np.float64)
+    a = synth.Stream(43).normal(40)
+    g, _ = mlp.loss_backward(blob, arch, p, a, np.zeros((40, 3)))
+    np.testing.assert_allclose(mlp.param_gradient(blob, arch, p, a), g, rtol=1e-12, atol=1e-14)
+
+
+def test_param_gradient_of_fourier_relu_network_matches_central_differences():
+    """sum_i a_i f(p_i) differentiated by central differences in sampled
+    parameters of every kind (B, W_l, b_l, w_out, b_out), at points whose
+    pre-activations all stay away from 0 (no ReLU decision changes within the
+    step)."""
+    arch = FFR
+    blob = synth.fourier_relu_init(arch, 44).astype(np.float64)
+    blob += 0.05 * synth.Stream(45).normal(blob.size)          # non-zero biases too
+    p = synth.uniform_cube(300, 46)[:, :3].astype(np.float64)
+    _, zs, _ = mlp.forward(blob, arch, p)
+    p = p[np.min([np.abs(z).min(axis=1) for z in zs], axis=0) > 1e-3]
+    assert len(p) > 10
+    a = synth.Stream(47).normal(len(p))
+    g = mlp.param_gradient(blob, arch, p, a)
+    idx = np.unique(synth.Stream(48).u64(60) % np.uint64(blob.size)).astype(np.int64)
+    idx = np.concatenate([idx, [0, 5, blob.size - 1, blob.size - 2]])   # B entries, w_out, b_out
+    h = 1e-6
+
+    def loss(b):
+        return a @ mlp.forward(b, arch, p)[0]
+
+    for i in idx:
+        bp, bm = blob.copy(), blob.copy()
+        bp[i] += h
+        bm[i] -= h
+        fd = (loss(bp) - loss(bm)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
