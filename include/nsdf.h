@@ -200,9 +200,11 @@ nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n,
  * activations with FP32 accumulation (cuBLAS); the other sums are FP32 and
  * reduced in a fixed order, so repeated calls give identical results.  Uses
  * about 2 n_hidden x width x 2 bytes of device memory per point, allocated on
- * the first call and when n grows.  FP32 contexts and Fourier-feature ReLU
- * networks: NSDF_ERR_UNSUPPORTED (use nsdf_backward for FP32 softplus
- * networks); n = 0: NSDF_ERR_INVALID_ARG.
+ * the first call and when n grows.  Fourier-feature ReLU contexts (Sec. 4.3)
+ * take the same route through their own tensor-core kernel; their
+ * frequencies B are not trained (random Fourier features) and receive 0.
+ * FP32 contexts: NSDF_ERR_UNSUPPORTED (use nsdf_backward); n = 0:
+ * NSDF_ERR_INVALID_ARG.
  */
 nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n,
                          const float *targets, float *g_weights, float *loss,

@@ -124,16 +124,27 @@ struct Epi {
   uint32_t a_ready;     // barrier a_ready[0]; a_ready[k] is 8 k bytes on
   int r, ch, lane;      // tile row (= TMEM lane); column group (kGroupCols of every atom)
   float px, py, pz;     // query point in the body frame
+  // training form: 16-bit rows [slot][n_pad][kW]; h_l in save_h slot l, the
+  // features in slot n_hidden, delta_l in save_d slot l; this thread's row
+  uint16_t *save_h, *save_d;
+  int64_t n_pad, row;
   __device__ __forceinline__ uint2 &bits(int l) const { return mask[(l * kColGroups + ch) * kM + r]; }
+  __device__ __forceinline__ void save(uint16_t *base, int slot, int c0, const uint32_t (&w)[kGroupCols / 2]) const {
+    if (row >= n_pad) return;   // the fully masked tiles past the last one
+    uint4 *dst = reinterpret_cast<uint4 *>(base + ((size_t)slot * n_pad + row) * kW + c0);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  }
 };
 
 // One chunk (kGroupCols columns) of a forward epilogue: z = D + b,
 // h = max(z, 0); the packed words of the next A operand go to `w` and the
 // slope bits are returned.  The last layer adds w_out . h to fpart and
 // writes delta = [z > 0] * w_out instead of h.
-template <bool kF16, bool LAST>
+template <bool kF16, bool LAST, bool kSave = false>
 __device__ __forceinline__ uint32_t fwd_chunk(int l, int c0, const uint32_t (&raw)[kGroupCols],
-                                              float &fpart, uint32_t (&w)[kGroupCols / 2]) {
+                                              float &fpart, uint32_t (&w)[kGroupCols / 2],
+                                              uint32_t (&hx)[kGroupCols / 2]) {
   uint32_t bits = 0;
 #pragma unroll
   for (int q = 0; q < kGroupCols / 4; ++q) {
@@ -142,13 +153,14 @@ __device__ __forceinline__ uint32_t fwd_chunk(int l, int c0, const uint32_t (&ra
     if (LAST) wo = lds4(kOffWout, c0 / 4 + q);
     const float bv[4] = {b.x, b.y, b.z, b.w};
     const float wv[4] = {wo.x, wo.y, wo.z, wo.w};
-    float v[4];
+    float v[4], hv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const float z = __uint_as_float(raw[4 * q + u]) + bv[u];
       const bool pos = z > 0.0f;
       bits |= (pos ? 1u : 0u) << (4 * q + u);
       const float h = pos ? z : 0.0f;
+      hv[u] = h;
       if (LAST) {
         fpart = fmaf(wv[u], h, fpart);
         v[u] = pos ? wv[u] : 0.0f;
@@ -158,6 +170,10 @@ __device__ __forceinline__ uint32_t fwd_chunk(int l, int c0, const uint32_t (&ra
     }
     w[2 * q] = pack16<kF16>(v[0], v[1]);
     w[2 * q + 1] = pack16<kF16>(v[2], v[3]);
+    if (LAST && kSave) {
+      hx[2 * q] = pack16<kF16>(hv[0], hv[1]);
+      hx[2 * q + 1] = pack16<kF16>(hv[2], hv[3]);
+    }
   }
   return bits;
 }
@@ -181,32 +197,46 @@ __device__ __forceinline__ void bwd_chunk(uint32_t bits, const uint32_t (&raw)[k
 __device__ __forceinline__ int chunk_col(const Epi &e, int k) { return kKAtom * k + kGroupCols * e.ch; }
 
 // Forward epilogue of layer l, product in TMEM columns dcol..dcol+255 (the
-// next chunk's TMEM load is issued while the current one is processed).
-template <bool kF16, bool LAST>
+// next chunk's TMEM load is issued while the current one is processed).  In
+// the training form the next A operand also goes to save_h slot l (h_l), or,
+// for the last layer, to save_d (delta_{L-1}) with h_{L-1} to save_h.
+template <bool kF16, bool LAST, bool kSave = false>
 __device__ __forceinline__ void fwd_product(const Epi &e, int l, uint32_t dcol, float &fpart) {
   const uint32_t t = e.t_row + dcol;
-  uint32_t ra[kGroupCols], rb[kGroupCols], bits[4], w[kGroupCols / 2];
+  uint32_t ra[kGroupCols], rb[kGroupCols], bits[4], w[kGroupCols / 2], hx[kGroupCols / 2];
+  auto keep = [&](int k) {
+    if constexpr (kSave) {
+      if (LAST) {
+        e.save(e.save_d, l, chunk_col(e, k), w);
+        e.save(e.save_h, l, chunk_col(e, k), hx);
+      } else {
+        e.save(e.save_h, l, chunk_col(e, k), w);
+      }
+    }
+  };
   tmem_ld16_async(t + chunk_col(e, 0), ra);
 #pragma unroll
   for (int k = 0; k < 4; k += 2) {
     tmem_wait_ld(ra);
     tmem_ld16_async(t + chunk_col(e, k + 1), rb);
-    bits[k] = fwd_chunk<kF16, LAST>(l, chunk_col(e, k), ra, fpart, w);
+    bits[k] = fwd_chunk<kF16, LAST, kSave>(l, chunk_col(e, k), ra, fpart, w, hx);
     store_a_cols(e.A, e.r, chunk_col(e, k), w);
     epi_arrive(e.a_ready + 8u * k, e.lane);
+    keep(k);
     tmem_wait_ld(rb);
     if (k + 2 < 4) tmem_ld16_async(t + chunk_col(e, k + 2), ra);
-    bits[k + 1] = fwd_chunk<kF16, LAST>(l, chunk_col(e, k + 1), rb, fpart, w);
+    bits[k + 1] = fwd_chunk<kF16, LAST, kSave>(l, chunk_col(e, k + 1), rb, fpart, w, hx);
     store_a_cols(e.A, e.r, chunk_col(e, k + 1), w);
     epi_arrive(e.a_ready + 8u * (k + 1), e.lane);
+    keep(k + 1);
   }
   if (!LAST) e.bits(l) = make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16));
 }
 
 // Reverse epilogue of layer l >= 1: delta_{l-1} = [z_{l-1} > 0] * g_{l-1};
 // m = the slope bits of layer l-1 (loaded before the product was awaited).
-template <bool kF16>
-__device__ __forceinline__ void bwd_product(const Epi &e, uint2 m, uint32_t dcol) {
+template <bool kF16, bool kSave = false>
+__device__ __forceinline__ void bwd_product(const Epi &e, uint2 m, int l, uint32_t dcol) {
   const uint32_t t = e.t_row + dcol;
   const uint32_t bits[4] = {m.x & 0xFFFFu, m.x >> 16, m.y & 0xFFFFu, m.y >> 16};
   uint32_t ra[kGroupCols], rb[kGroupCols], w[kGroupCols / 2];
@@ -218,19 +248,21 @@ __device__ __forceinline__ void bwd_product(const Epi &e, uint2 m, uint32_t dcol
     bwd_chunk<kF16>(bits[k], ra, w);
     store_a_cols(e.A, e.r, chunk_col(e, k), w);
     epi_arrive(e.a_ready + 8u * k, e.lane);
+    if constexpr (kSave) e.save(e.save_d, l - 1, chunk_col(e, k), w);   // delta_{l-1}
     tmem_wait_ld(rb);
     if (k + 2 < 4) tmem_ld16_async(t + chunk_col(e, k + 2), ra);
     bwd_chunk<kF16>(bits[k + 1], rb, w);
     store_a_cols(e.A, e.r, chunk_col(e, k + 1), w);
     epi_arrive(e.a_ready + 8u * (k + 1), e.lane);
+    if constexpr (kSave) e.save(e.save_d, l - 1, chunk_col(e, k + 1), w);
   }
 }
 
 // gamma(p) for the thread's 2 x kGroupCols frequencies
 // j = 64 blk + kGroupCols ch + i: in the permuted column order their sines
 // are chunk 2 blk and their cosines chunk 2 blk + 1 of this thread.
-template <bool kF16>
-__device__ __forceinline__ void feature_stage(const Epi &e) {
+template <bool kF16, bool kSave = false>
+__device__ __forceinline__ void feature_stage(const Epi &e, int L) {
 #pragma unroll 1
   for (int blk = 0; blk < 2; ++blk) {
     uint32_t sw[kGroupCols / 2], cw[kGroupCols / 2];
@@ -248,6 +280,10 @@ __device__ __forceinline__ void feature_stage(const Epi &e) {
     epi_arrive(e.a_ready + 16u * blk, e.lane);
     store_a_cols(e.A, e.r, chunk_col(e, 2 * blk + 1), cw);
     epi_arrive(e.a_ready + 16u * blk + 8u, e.lane);
+    if constexpr (kSave) {
+      e.save(e.save_h, L, chunk_col(e, 2 * blk), sw);
+      e.save(e.save_h, L, chunk_col(e, 2 * blk + 1), cw);
+    }
   }
 }
 
@@ -299,7 +335,9 @@ __device__ __forceinline__ TileRef tile_ref(const QueryParams &prm, int64_t t) {
   return TileRef{lo, prm.g_offsets[lo] + lt * kM, prm.g_counts[lo] - lt * kM};
 }
 
-template <bool kF16>
+// kSave: the training form, which also writes every A operand out
+// (QueryParams::save_h / save_d; single-network launches only).
+template <bool kF16, bool kSave = false>
 __global__ void __launch_bounds__(kThreads, 1)
     query_tc16_ff_kernel(const __grid_constant__ QueryParams prm, const __grid_constant__ CUtensorMap tmap_fwd,
                          const __grid_constant__ CUtensorMap tmap_bwd) {
@@ -461,6 +499,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     e.r = r;
     e.ch = ch;
     e.lane = lane;
+    e.save_h = prm.save_h;
+    e.save_d = prm.save_d;
+    e.n_pad = (prm.n + kM - 1) / kM * kM;
     uint32_t d_phase = 0, x_phase = 0, w_phase = 0;
     int cur_net = -1;
     float bout = 0.f;
@@ -516,6 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const bool valid = r < tr.valid;
       const int64_t idx = tr.first + r;
+      e.row = idx;
       float4 pw = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid) pw = prm.pts[idx];
       e.px = pw.x; e.py = pw.y; e.pz = pw.z;
@@ -530,19 +572,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       auto dcol = [](int g) { return (uint32_t)(kN * (g & 1)); };
 
       // ---- gamma(p), the first A operand ----
-      feature_stage<kF16>(e);
+      feature_stage<kF16, kSave>(e, L);
 
       // ---- layers 0 .. L-1 (forward): product l ----
       for (int l = 0; ok && l < L; ++l) {
         if (!wait_product()) { fail(); ok = false; break; }
-        if (l == L - 1) fwd_product<kF16, true>(e, l, dcol(l), fpart);
-        else fwd_product<kF16, false>(e, l, dcol(l), fpart);
+        if (l == L - 1) fwd_product<kF16, true, kSave>(e, l, dcol(l), fpart);
+        else fwd_product<kF16, false, kSave>(e, l, dcol(l), fpart);
       }
       // ---- Jacobian-transpose chain: layers L-1 .. 1, product 2L-1-l ----
       for (int l = L - 1; ok && l >= 1; --l) {
         const uint2 m = e.bits(l - 1);    // in flight while the product is awaited
         if (!wait_product()) { fail(); ok = false; break; }
-        bwd_product<kF16>(e, m, dcol(G - 1 - l));
+        bwd_product<kF16, kSave>(e, m, l, dcol(G - 1 - l));
       }
       if (!ok) break;
       // ---- layer 0 (product 2L-1): g_gamma through the feature Jacobian ----
@@ -629,7 +671,7 @@ int resident_cluster_ctas(int num_sms) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev] < num_sms ? cached[dev] : num_sms;
-  cudaFuncSetAttribute(query_tc16_ff_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaFuncSetAttribute(query_tc16_ff_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kCluster * 256, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
@@ -642,7 +684,7 @@ int resident_cluster_ctas(int num_sms) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, query_tc16_ff_kernel<false>, &cfg) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveClusters(&clusters, query_tc16_ff_kernel<false, false>, &cfg) != cudaSuccess ||
       clusters < 1) {
     cudaGetLastError();
     clusters = num_sms / kCluster;
@@ -652,9 +694,9 @@ int resident_cluster_ctas(int num_sms) {
   return ctas < num_sms ? ctas : num_sms;
 }
 
-template <bool kF16>
+template <bool kF16, bool kSave>
 cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(query_tc16_ff_kernel<kF16>,
+  cudaError_t e = cudaFuncSetAttribute(query_tc16_ff_kernel<kF16, kSave>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   // grouped: p.n = the largest point index + 1; every network may add a
@@ -674,7 +716,7 @@ cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cu
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, query_tc16_ff_kernel<kF16>, p, net.tmap_fwd, net.tmap_bwd);
+  e = cudaLaunchKernelEx(&cfg, query_tc16_ff_kernel<kF16, kSave>, p, net.tmap_fwd, net.tmap_bwd);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -712,7 +754,11 @@ int query_tc16_ff_grouped_grid(int64_t max_tiles, int num_sms) {
 cudaError_t launch_query_tc16_ff(const QueryParams &p, const NetDevice &net, bool fp16, int num_sms,
                                  cudaStream_t s) {
   if (!query_tc16_ff_supported(p.width, p.n_hidden, p.ff, p.relu)) return cudaErrorInvalidValue;
-  return fp16 ? launch_t<true>(p, net, num_sms, s) : launch_t<false>(p, net, num_sms, s);
+  if (p.save_h) {
+    if (p.g_nets > 0 || !p.save_d) return cudaErrorInvalidValue;
+    return fp16 ? launch_t<true, true>(p, net, num_sms, s) : launch_t<false, true>(p, net, num_sms, s);
+  }
+  return fp16 ? launch_t<true, false>(p, net, num_sms, s) : launch_t<false, false>(p, net, num_sms, s);
 }
 
 }  // namespace nsdf

@@ -14,6 +14,12 @@
 // accumulation), and the remaining sums (biases, W_0 on p, the skip layer's
 // columns on p / sqrt(2), w_out and b_out) are FP32 per-block partial sums
 // reduced in block order, so the result does not depend on scheduling.
+//
+// Fourier-feature ReLU networks (Sec. 4.3) take the same route with their own
+// tensor-core kernel: layer 0 is a 256 x 256 product too, its input (the
+// features, saved in the kernel's permuted column order) gets its own GEMM,
+// whose columns are put back in feature order; the frequencies B are not
+// trained (random Fourier features) and get a zero gradient.
 
 #include <cublas_v2.h>
 
@@ -32,6 +38,7 @@ constexpr float kInvSqrt2 = 0.70710678118654752f;
 // Blob offsets of every layer (the layout of nsdf_num_params).
 struct BlobPlan {
   int L, W, skip;
+  int ff;                       // Fourier frequencies m (0: none)
   int64_t woff[66], boff[66];   // layers 0..L, then woff[L+1] = the blob size
   int out[66];
 };
@@ -100,15 +107,15 @@ __device__ __forceinline__ float2 unpack16(uint32_t w, int fp16) {
 
 // Per-block partial sums over kRowsPerBlock points, for job j = blockIdx.y:
 //   j <  L : sum_i delta_j(i)[c]                         (bias of layer j)
-//   j == L : sum_i delta_0(i)[c] p_i[k], k = 0..2         (W_0)
+//   j == L : sum_i delta_0(i)[c] p_i[k], k = 0..2         (W_0; not for ff)
 //   j == L+1: sum_i delta_s(i)[c] p_i[k] / sqrt(2)        (skip layer s, its p columns)
 //   j == L+2: sum_i a_i h_{L-1}(i)[c]; and sum_i a_i      (w_out, b_out)
 // Thread t covers columns 8t .. 8t+7 (one 16-byte load per row); part[j][block][c][3].
 __global__ void small_partials_kernel(const uint16_t *__restrict__ save_h,
                                       const uint16_t *__restrict__ save_d,
                                       const float4 *__restrict__ pts, const float *__restrict__ a,
-                                      int L, int W, int skip, int64_t n, int64_t n_pad, int fp16,
-                                      float *__restrict__ part) {
+                                      int L, int W, int skip, int ff, int64_t n, int64_t n_pad,
+                                      int fp16, float *__restrict__ part) {
   const int j = blockIdx.y;
   const int c = 8 * threadIdx.x;
   if (c >= W) return;
@@ -117,7 +124,7 @@ __global__ void small_partials_kernel(const uint16_t *__restrict__ save_h,
   if (r1 > n_pad) r1 = n_pad;
   const uint16_t *src = nullptr;
   if (j < L) src = save_d + (size_t)j * n_pad * W;
-  else if (j == L) src = save_d;
+  else if (j == L) src = ff ? nullptr : save_d;
   else if (j == L + 1) src = skip > 0 ? save_d + (size_t)skip * n_pad * W : nullptr;
   else src = save_h + (size_t)(L - 1) * n_pad * W;
   float acc[8][3];
@@ -185,6 +192,10 @@ __global__ void scatter_grad_kernel(const float *__restrict__ G, const float *__
   auto sm = [&](int j, int c, int k) { return small[j * per_job + (int64_t)c * 3 + k]; };
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < plan.woff[0]) {                       // the frequencies B: not trained
+      g[t] = 0.f;
+      continue;
+    }
     int l = 0;
     while (l < L && t >= plan.woff[l + 1]) ++l;   // layer of element t
     float v;
@@ -193,7 +204,17 @@ __global__ void scatter_grad_kernel(const float *__restrict__ G, const float *__
       v = l < L ? sm(l, nn, 0) : sm(L + 2, 0, 2);
     } else {
       const int64_t e = t - plan.woff[l];
-      if (l == 0) {
+      if (plan.ff > 0 && l < L) {
+        // G_l[n][c] for every layer; layer 0's columns are in the kernel's
+        // feature order: feature k = s m + 64 g + i sits in column 128 g + 64 s + i
+        const int nn = (int)(e / W), k = (int)(e % W);
+        int c = k;
+        if (l == 0) {
+          const int sgn = k / plan.ff, j = k % plan.ff;
+          c = 128 * (j / 64) + 64 * sgn + (j % 64);
+        }
+        v = G[((size_t)l * W + nn) * W + c];
+      } else if (l == 0) {
         v = sm(L, (int)(e / 3), (int)(e % 3));
       } else if (l == L) {
         v = sm(L + 2, (int)e, 0);
@@ -268,7 +289,7 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
   nsdf_status st = ctx_query_setup(ctx, &p, &num_sms, &W, &L, &tc16, &fp16, &net);
   if (st != NSDF_OK) return st;
   if (!tc16) return NSDF_ERR_UNSUPPORTED;   // FP32 contexts: nsdf_backward
-  if (p.ff > 0 || p.relu) return NSDF_ERR_UNSUPPORTED;   // softplus networks only
+  const bool ff = p.ff > 0;                  // the Fourier-feature ReLU kernel
   if (n == 0) return NSDF_ERR_INVALID_ARG;
   if (!pts || !targets) return NSDF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(pts) & 15u) || (reinterpret_cast<uintptr_t>(g_weights) & 3u) ||
@@ -286,11 +307,14 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
     cudaStreamSynchronize(s);
     free_all(t);
     const size_t rows = (size_t)n_pad;
-    bool ok = dalloc(&t->save_h, (size_t)L * rows * W) && dalloc(&t->save_d, (size_t)L * rows * W) &&
+    // ff: h_0 .. h_{L-1} and the features (slot L); G for every layer
+    const size_t hslots = ff ? (size_t)L + 1 : (size_t)L;
+    const size_t gslots = ff ? (size_t)L : (size_t)(L > 1 ? L - 1 : 1);
+    bool ok = dalloc(&t->save_h, hslots * rows * W) && dalloc(&t->save_d, (size_t)L * rows * W) &&
               dalloc(&t->ns, rows) && dalloc(&t->a, rows) &&
               dalloc(&t->loss_part, (rows + 255) / 256) &&
               dalloc(&t->part, (size_t)jobs * nb * W * 3) && dalloc(&t->small, (size_t)jobs * W * 3) &&
-              dalloc(&t->G, (size_t)(L > 1 ? L - 1 : 1) * W * W) && dalloc(&t->loss_tmp, 1);
+              dalloc(&t->G, gslots * W * W) && dalloc(&t->loss_tmp, 1);
     if (!ok) {
       free_all(t);
       return NSDF_ERR_OOM;
@@ -310,7 +334,8 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
   p.save_d = t->save_d;
   st = ctx_query_scratch(ctx, n, &p);
   if (st != NSDF_OK) return st;
-  cudaError_t e = launch_query_tc16_net(p, *net, fp16, num_sms, s);
+  cudaError_t e = ff ? launch_query_tc16_ff(p, *net, fp16, num_sms, s)
+                     : launch_query_tc16_net(p, *net, fp16, num_sms, s);
   if (e != cudaSuccess) return NSDF_ERR_CUDA;
   // 2. a_i and the loss; delta rows times a_i
   const int lb = (int)((n_pad + 255) / 256);
@@ -323,18 +348,22 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
   if (cublasSetStream(t->blas, s) != CUBLAS_STATUS_SUCCESS) return NSDF_ERR_CUDA;
   const cudaDataType_t dt = fp16 ? CUDA_R_16F : CUDA_R_16BF;
   const float one = 1.f, zero = 0.f;
-  for (int l = 1; l < L; ++l) {
-    const uint16_t *H = t->save_h + (size_t)(l - 1) * n_pad * W;
+  for (int l = ff ? 0 : 1; l < L; ++l) {
+    // layer l reads h_{l-1} (for ff layer 0: the features, slot L)
+    const int hs = (ff && l == 0) ? L : l - 1;
+    const uint16_t *H = t->save_h + (size_t)hs * n_pad * W;
     const uint16_t *D = t->save_d + (size_t)l * n_pad * W;
+    float *Gl = t->G + (size_t)(ff ? l : l - 1) * W * W;
     // column-major: C (W x W) = H^T-view (W x n_pad) * D-view^T (n_pad x W)
     if (cublasGemmEx(t->blas, CUBLAS_OP_N, CUBLAS_OP_T, W, W, (int)n_pad, &one, H, dt, W, D, dt, W,
-                     &zero, t->G + (size_t)(l - 1) * W * W, CUDA_R_32F, W, CUBLAS_COMPUTE_32F,
+                     &zero, Gl, CUDA_R_32F, W, CUBLAS_COMPUTE_32F,
                      CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
       return NSDF_ERR_CUDA;
   }
   // 4. the small sums, reduced in block order
   small_partials_kernel<<<dim3(nb, jobs), W / 8, 0, s>>>(t->save_h, t->save_d, p.pts, t->a, L, W,
-                                                         p.skip, n, n_pad, fp16 ? 1 : 0, t->part);
+                                                         p.skip, p.ff, n, n_pad, fp16 ? 1 : 0,
+                                                         t->part);
   const int64_t nsmall = (int64_t)jobs * W * 3;
   small_reduce_kernel<<<(int)((nsmall + 255) / 256), 256, 0, s>>>(t->part, jobs, nb, W, t->small);
   // 5. scatter into the blob layout
@@ -342,6 +371,7 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
   plan.L = L;
   plan.W = W;
   plan.skip = p.skip;
+  plan.ff = p.ff;
   const int64_t total = ctx_blob_offsets(ctx, plan.woff, plan.boff, plan.out);
   plan.woff[L + 1] = total;
   scatter_grad_kernel<<<4 * num_sms, 256, 0, s>>>(t->G, t->small, plan, total, 1.0f / (float)n,

@@ -30,7 +30,8 @@ class MeshFit:
         self.eikonal = eikonal
         self.sample_seed = sample_seed
         self.net = NeuralSDF(arch, NSDF_FP32)
-        self.blob = torch.from_numpy(synth.geometric_init(arch, init_seed)).cuda().requires_grad_(True)
+        init = synth.fourier_relu_init if getattr(arch, "ff_freqs", 0) > 0 else synth.geometric_init
+        self.blob = torch.from_numpy(init(arch, init_seed)).cuda().requires_grad_(True)
         self.opt = torch.optim.Adam([self.blob], lr=lr)
         self.sched = torch.optim.lr_scheduler.StepLR(self.opt, lr_halving, 0.5)
         self.Vd = torch.from_numpy(self.V.astype(np.float32)).cuda().contiguous()
@@ -101,7 +102,8 @@ def penalty_gradient(net, blob, pts, eps):
 
 
 class MeshFitTC:
-    """Fitting the 512-wide body-scale network on the 16-bit tensor-core path.
+    """Fitting the 512-wide body-scale network, or one of the paper's
+    Fourier-feature ReLU networks (Sec. 4.3), on the 16-bit tensor-core path.
 
     As in the paper (Sec. 3.1, Sec. 4.3), the training set is sampled once: a
     pool of seeded points (80% near the surface, 20% uniform) with exact
@@ -118,7 +120,8 @@ class MeshFitTC:
         self.batch = batch
         self.sample_seed = sample_seed
         self.net = NeuralSDF(arch, precision)
-        self.blob = torch.from_numpy(synth.geometric_init(arch, init_seed)).cuda().requires_grad_(True)
+        init = synth.fourier_relu_init if getattr(arch, "ff_freqs", 0) > 0 else synth.geometric_init
+        self.blob = torch.from_numpy(init(arch, init_seed)).cuda().requires_grad_(True)
         self.opt = torch.optim.Adam([self.blob], lr=lr)
         self.sched = torch.optim.lr_scheduler.StepLR(self.opt, lr_halving, 0.5)
         Vd = torch.from_numpy(np.asarray(V, dtype=np.float32)).cuda().contiguous()

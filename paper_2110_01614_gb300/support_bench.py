@@ -24,9 +24,11 @@
 * fit512: the 512-wide body-scale network fitted with the paper's L1 loss on
   the BF16 tensor-core path (pool of 1,048,576 points with exact targets,
   batches of 250,000): seconds per step and the time of nsdf_l1_grad alone.
+* fit_paper: the same for the paper's dragon-shaped Fourier-feature ReLU
+  network.
 
 Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped grouped_paper cloth
-                                                      paper_arch fit512]
+                                                      paper_arch fit512 fit_paper]
 """
 
 import json
@@ -207,14 +209,39 @@ def bench_fit512(steps=20):
             "loss_first": losses[0], "loss_last": losses[-1]}
 
 
+def bench_fit_paper(steps=20):
+    """The paper's dragon-shaped network (Fourier features + 8 ReLU layers of
+    256) fitted with the L1 loss on the BF16 tensor-core path: pool of
+    1,048,576 points with exact targets, batches of 250,000."""
+    from . import nsdf_l1_grad
+    from .fit import MeshFitTC
+    arch = synth.Arch(3, 256, 8, -1, 100.0, "relu", 128)
+    V, F = synth.displaced_icosphere(level=5, seed=7)
+    fit = MeshFitTC(arch, V, F, precision=NSDF_BF16, pool_points=1 << 20, batch=250_000)
+    fit.run(2)
+    losses, s_per_step = fit.run(steps)
+    P, d = fit.pool_P[:250_000], fit.pool_d[:250_000]
+    ms = events_ms(lambda: nsdf_l1_grad(fit.net.ctx, P, d, fit.grad, fit.loss), 5)
+    fit.close()
+    # algorithmic work of the gradient: the query's forward and J^T products
+    # (2 x 8 x 256^2 + 256 MAC per point) plus the weight-gradient products
+    # (8 x 256^2 MAC per point)
+    mac = 3 * 8 * 256 * 256 + 256
+    return {"workload": "fit_paper", "shape": "dragon_8x256", "precision": "bf16", "batch": 250_000,
+            "pool": 1 << 20, "s_per_step": s_per_step, "l1_grad_ms": ms,
+            "l1_grad_tflops": 2 * mac * 250_000 / (ms * 1e-3) / 1e12,
+            "loss_first": losses[0], "loss_last": losses[-1]}
+
+
 def main(argv):
-    which = argv or ["fit", "penalty", "grouped", "grouped_paper", "cloth", "paper_arch", "fit512"]
+    which = argv or ["fit", "penalty", "grouped", "grouped_paper", "cloth", "paper_arch", "fit512",
+                     "fit_paper"]
     torch.cuda.set_device(0)
     for w in which:
         t0 = time.perf_counter()
         r = {"fit": bench_fit, "penalty": bench_penalty, "grouped": bench_grouped,
              "grouped_paper": bench_grouped_paper, "cloth": bench_cloth,
-             "paper_arch": bench_paper_arch, "fit512": bench_fit512}[w]()
+             "paper_arch": bench_paper_arch, "fit512": bench_fit512, "fit_paper": bench_fit_paper}[w]()
         r["wall_s"] = time.perf_counter() - t0
         print(json.dumps(r), flush=True)
 

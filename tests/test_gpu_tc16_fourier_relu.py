@@ -327,3 +327,79 @@ def test_grouped_graph_replays_with_new_counts_and_poses(nsdf):
             assert np.abs(got[sl, 3] - f_r).max() <= 24 * U["bf16"]
     nsdf.nsdf_sync_status(s.ctx)
     s.close()
+
+
+# ---- fitting (Sec. 3.1, L1 loss) of the paper's networks on tensor cores ----
+
+def layer_blocks(arch):
+    """(name, slice) of every weight matrix and bias of a blob (B excluded)."""
+    from synth.weights import layer_shapes
+    out, off = [], arch.ff_freqs * 3
+    for l, (o, i) in enumerate(layer_shapes(arch)):
+        out.append((f"W{l}", slice(off, off + o * i)))
+        off += o * i
+        out.append((f"b{l}", slice(off, off + o)))
+        off += o
+    return out
+
+
+def l1_problem(arch, n, seed):
+    blob = synth.fourier_relu_init(arch, seed)
+    pts = synth.body_scale_points(n, seed + 1)
+    f, _, _ = mlp.forward(blob, arch, pts[:, :3])
+    s = synth.Stream(seed + 2)
+    off = s.uniform(n, 0.05, 0.2) * np.where(s.uniform(n) < 0.5, -1.0, 1.0)
+    d = (f + off).astype(np.float32)
+    a = np.sign(f - d.astype(np.float64)) / n
+    return blob, pts, d, a, np.abs(f - d).mean()
+
+
+def gpu_l1_grad(nsdf, fmt, arch, blob, pts, d):
+    s = nsdf.NeuralSDF(arch, P(nsdf, fmt)).load(blob)
+    g = torch.full((blob.size,), 7.0, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    nsdf.nsdf_l1_grad(s.ctx, torch.from_numpy(pts).cuda(), torch.from_numpy(d).cuda(), g, loss)
+    nsdf.nsdf_sync_status(s.ctx)
+    s.close()
+    return g.cpu().numpy().astype(np.float64), float(loss.cpu())
+
+
+# Per-layer bounds (relative Frobenius norm).  Against the 16-bit oracle the
+# kernel differs only where the accumulation order (or a feature's hardware
+# sine) flips a ReLU decision, at a few percent of the points, each flip
+# moving that point's whole contribution: measured up to 2.4e-2 on the
+# 8-layer network; bound 5e-2.  Against the exact gradient the 16-bit
+# decisions themselves add up to 0.13 (BF16) and 0.05 (FP16) on 8 layers
+# (tests/test_oracle_rounded.py pins the 4-layer case): bounds 0.25 and 0.1.
+GRAD_TOL_ROUNDED = 5e-2
+GRAD_TOL_EXACT = {"bf16": 0.25, "fp16": 0.1}
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+@pytest.mark.parametrize("arch", [BUNNY, DRAGON], ids=["4x256", "8x256"])
+def test_l1_grad_against_oracles(nsdf, fmt, arch):
+    """nsdf_l1_grad of a Fourier-feature ReLU context: 1000 points (eight tiles
+    and a ragged tail), targets 0.05-0.2 from f (beyond the 16-bit sdf error,
+    so sign(f - d) is the same decision on both sides)."""
+    blob, pts, d, a, loss_ref = l1_problem(arch, 1000, 70)
+    g, loss = gpu_l1_grad(nsdf, fmt, arch, blob, pts, d)
+    g_r = rounded.l1_grad_ff_relu(blob, arch, pts[:, :3], a, fmt)
+    g_x = mlp.param_gradient(blob, arch, pts[:, :3], a)
+    assert np.all(g[: arch.ff_freqs * 3] == 0.0)            # B is not trained
+    assert abs(loss - loss_ref) <= 1e-3 * loss_ref + 24 * U[fmt]
+    worst_r = worst_x = 0.0
+    for name, sl in layer_blocks(arch):
+        nr = np.linalg.norm(g_r[sl])
+        worst_r = max(worst_r, np.linalg.norm(g[sl] - g_r[sl]) / nr)
+        worst_x = max(worst_x, np.linalg.norm(g[sl] - g_x[sl]) / np.linalg.norm(g_x[sl]))
+    print(fmt, arch.n_hidden, "worst layer vs rounded %.3e, vs exact %.3e" % (worst_r, worst_x))
+    assert worst_r <= GRAD_TOL_ROUNDED
+    assert worst_x <= GRAD_TOL_EXACT[fmt]
+
+
+def test_l1_grad_is_deterministic(nsdf):
+    blob, pts, d, _, _ = l1_problem(BUNNY, 3000, 80)
+    g1, l1 = gpu_l1_grad(nsdf, "bf16", BUNNY, blob, pts, d)
+    g2, l2 = gpu_l1_grad(nsdf, "bf16", BUNNY, blob, pts, d)
+    np.testing.assert_array_equal(g1, g2)
+    assert l1 == l2
