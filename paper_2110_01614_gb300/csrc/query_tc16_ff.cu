@@ -6,8 +6,9 @@
 //
 // One persistent CTA per SM walks tiles of 128 points.  Per tile the whole
 // query of Sec. 3.2 runs on chip:
-//   * the epilogue warps evaluate gamma(p) on CUDA cores (compensated phase,
-//     sinpi / cospi; see ff_phase.cuh) and write it as the first A operand,
+//   * the epilogue warps evaluate gamma(p) on CUDA cores (FMA phase with its
+//     integer part removed exactly, hardware sine and cosine; ff_sincos16 in
+//     ff_phase.cuh) and write it as the first A operand,
 //   * every layer z_l = W_l x_l (Eq. 1; layer 0 reads gamma(p)) is 16
 //     tcgen05.mma (M=128, N=256, K=16; 16-bit x 16-bit -> FP32) into TMEM,
 //     A = the 128 x 256 activation tile in shared memory (128-byte swizzled
@@ -27,9 +28,13 @@
 //     FP32: grad f = 2 pi sum_j (g_sin,j cos(2 pi b_j.p) - g_cos,j sin(2 pi b_j.p)) b_j,
 //   * Eq. 2, the test f < eps and the contact point of Eq. 3 (with the rigid
 //     transform of Sec. 4.2) in the final epilogue; float4 stores.
-// Within a tile each product and its epilogue run back to back (a product
-// needs the whole previous epilogue); the weight ring fetches the next
-// product's panels while the epilogue runs.
+//
+// Hand-over: TMEM holds two products (2 x 256 columns), so product g + 1
+// may run while the epilogue still reads product g; the epilogue writes the
+// next A operand K atom by K atom (64 columns) and announces each atom on its
+// own barrier, so the next product starts on atom 0 once a quarter of the
+// epilogue is done.  The weight ring fetches the next product's panels
+// meanwhile.
 //
 // The feature tile uses a permuted column order so that each epilogue thread
 // evaluates each of its phases once and uses both its sine and its cosine:
@@ -37,10 +42,19 @@
 // frequency j = 64 g + i (ff_feature_of_column); layer 0's weights are packed
 // with their columns in that order, and its transposed copy with its rows.
 //
-// Warp roles (384 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
-// TMEM owner, warps 2, 3 idle, warps 4..11 = epilogue (warp w reads TMEM
-// lanes 32*(w%4)..+31; warps 4..7 take columns 0..127 of every product,
-// warps 8..11 columns 128..255).  Every wait is bounded
+// Grouped launches (QueryParams::g_nets > 0) walk a device-built tile list in
+// which every body's tiles start on an even index and come in pairs, so that
+// the two CTAs of a cluster always share one network's weight panels; the
+// tensor maps cover every network of the context (body k at rows
+// k * n_hidden * 256), and the epilogue warps reload the small weights and
+// the pose when the body changes.  The training form (kSave) also writes the
+// features, every h_l and every delta_l out as 16-bit rows for the
+// weight-gradient products of the fitting loss (train.cu).
+//
+// Warp roles (640 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
+// TMEM owner, warps 2, 3 idle, warps 4..19 = epilogue (warp w reads TMEM
+// lanes 32*(w%4)..+31; the four warps of column group g = (w - 4) / 4 take
+// columns 16 g .. 16 g + 15 of every K atom).  Every wait is bounded
 // (QueryParams::wait_budget clock cycles); on expiry the kernel records
 // kDevTimeout, drains what it has in flight and returns.
 
