@@ -370,8 +370,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t a_ready = bar0 + 8u * (2 * kStages);
   const uint32_t d_full = a_ready + 8u * kAtoms;        // MMA -> epilogue: the product is in TMEM
   const uint32_t mma_done = d_full + 8u;
-  const uint32_t x_full = mma_done + 8u;    // columns 128..255 have published their partial sums
-  const uint32_t x_empty = x_full + 8u;     // columns 0..127 have consumed them
+  const uint32_t x_full = mma_done + 8u;    // column groups 1.. have published their partial sums
+  const uint32_t x_empty = x_full + 8u;     // column group 0 has consumed them
   // epilogue warps: done with the small weights of the previous network /
   // the next network's small weights are in shared memory
   const uint32_t w_free = x_empty + 8u;
