@@ -11,8 +11,9 @@
   its own network of the paper's dragon shape (Fourier features + 8 ReLU
   layers of 256), BF16 tensor cores against the FP32 grouped kernel.
 * cloth: 1024 x 1024 cloth, per-step time of Verlet + collision solve for the
-  body-scale network in BF16 / FP16 / FP32, and of the exact brute-force mesh
-  SDF of every vertex (20,480 triangles) as the plain reference.
+  body-scale network in BF16 / FP16 / FP32 and for the paper's dragon-shaped
+  network in BF16, and of the exact brute-force mesh SDF of every vertex
+  (20,480 triangles) as the plain reference.
 
 * paper_arch: the paper's own network shapes (Sec. 4.3: a Fourier-feature
   layer of 128 frequencies, then 8 (dragon) or 4 (bunny) ReLU layers of 256
@@ -160,6 +161,13 @@ def bench_cloth(steps=20):
         ts = sim.run(body, steps if name != "fp32" else 3)
         res[f"{name}_ms_per_step"] = statistics.median(ts)
         body.close()
+    # the same cloth against the paper's dragon-shaped network (Sec. 4.3) in BF16
+    ff = synth.Arch(3, 256, 8, -1, 100.0, "relu", 128)
+    body = NeuralSDF(ff, NSDF_BF16).load(synth.fourier_relu_init(ff, 0))
+    sim = ClothSim(n=1024)
+    sim.run(body, 2)
+    res["paper_dragon_bf16_ms_per_step"] = statistics.median(sim.run(body, steps))
+    body.close()
     V, F = synth.displaced_icosphere(level=5, seed=7)
     sim = ClothSim(n=1024)
     ms, _ = mesh_reference_step_ms(V, F, sim.x, repeats=2)
