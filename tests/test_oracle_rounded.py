@@ -34,7 +34,7 @@ def blob_of(B, layers):
 def test_round16_matches_library_conversions():
     s = synth.Stream(21)
     x = s.normal(20000, std=3.0).astype(np.float32)
-    # exact ties and near-ties around 1 for both formats, signed
+    # exact ties and near-ties next to 1.0 for both formats, both signs
     ties = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11,
                      1 + 2.0 ** -8 + 2.0 ** -20, 2.0 ** -130, 65504.0, 1e-6], dtype=np.float32)
     x = np.concatenate([x, ties, -ties]).astype(np.float32)
