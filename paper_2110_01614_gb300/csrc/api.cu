@@ -288,7 +288,15 @@ nsdf_status set_transform(const float *T, QueryParams &p) {
 
 nsdf_status ensure_pipeline(nsdf_ctx *ctx) {
   if (ctx->stage) return NSDF_OK;
-  const int64_t chunk = 1 << 18;
+  // about 256K points per chunk; the tensor-core kernels (one 128-point tile
+  // per CTA and iteration) get a whole number of grid-wide iterations, so no
+  // chunk ends in a partly filled wave of tiles
+  int64_t chunk = 1 << 18;
+  if (use_bf16(ctx)) {
+    const int64_t wave = (int64_t)query_grid(ctx, chunk) * 128;
+    const int64_t waves = (chunk + wave / 2) / wave;
+    chunk = (waves > 0 ? waves : 1) * wave;
+  }
   cudaError_t e;
   for (int i = 0; i < 2; ++i) {
     e = cudaStreamCreateWithFlags(&ctx->pipe[i], cudaStreamNonBlocking);
