@@ -403,3 +403,25 @@ def test_l1_grad_is_deterministic(nsdf):
     g2, l2 = gpu_l1_grad(nsdf, "bf16", BUNNY, blob, pts, d)
     np.testing.assert_array_equal(g1, g2)
     assert l1 == l2
+
+
+def test_host_buffers_equal_device_buffers(nsdf):
+    """The host-buffer pipeline (chunks on two streams, sized to whole waves of
+    tiles) gives bitwise the results of one device-buffer launch: 300,000
+    points, one full chunk and a partial one."""
+    n = 300_000
+    blob = synth.fourier_relu_init(DRAGON, 90)
+    pts = torch.from_numpy(synth.body_scale_points(n, 91)).pin_memory()
+    s = nsdf.NeuralSDF(DRAGON, nsdf.NSDF_BF16).load(blob)
+    h_out, h_ns = torch.empty_like(pts).pin_memory(), torch.empty_like(pts).pin_memory()
+    h_hit = torch.empty(n, dtype=torch.uint8).pin_memory()
+    nsdf.nsdf_collide(s.ctx, pts, EPS, h_out, h_ns, h_hit)
+    d = pts.cuda()
+    d_out, d_ns = torch.empty_like(d), torch.empty_like(d)
+    d_hit = torch.empty(n, dtype=torch.uint8, device="cuda")
+    nsdf.nsdf_collide(s.ctx, d, EPS, d_out, d_ns, d_hit)
+    torch.cuda.synchronize()
+    nsdf.nsdf_sync_status(s.ctx)
+    s.close()
+    assert torch.equal(h_out, d_out.cpu()) and torch.equal(h_ns, d_ns.cpu())
+    assert torch.equal(h_hit, d_hit.cpu())
