@@ -22,8 +22,17 @@ from .autograd import sdf_query
 
 
 class MeshFit:
+    """FP32 fitting with the hand-written backward (L1 + eikonal).
+
+    pool_points=None draws fresh seeded training points every step (the
+    targets from the brute-force mesh kernel each time); pool_points=N samples
+    N points once, as the paper does (Sec. 3.1 samples a fixed set per shape),
+    computes their targets once, and draws a seeded batch of n_points from the
+    pool every step.
+    """
+
     def __init__(self, arch, V, F, n_points=250_000, lr=1e-3, eikonal=0.1, init_seed=0,
-                 sample_seed=1000, lr_halving=500):
+                 sample_seed=1000, lr_halving=500, pool_points=None):
         self.arch = arch
         self.V, self.F = np.asarray(V), np.asarray(F)
         self.n_points = n_points
@@ -37,16 +46,30 @@ class MeshFit:
         self.Vd = torch.from_numpy(self.V.astype(np.float32)).cuda().contiguous()
         self.Fd = torch.from_numpy(self.F.astype(np.int32)).cuda().contiguous()
         self.step_index = 0
+        self.pool_points = pool_points
+        if pool_points:
+            self.pool_P = torch.from_numpy(
+                synth.training_points(self.V, self.F, pool_points, sample_seed)).cuda()
+            self.pool_d = self.targets(self.pool_P)
 
     def targets(self, P):
         d = torch.empty(P.shape[0], device="cuda")
         nsdf_mesh_sdf(self.Vd, self.Fd, P, d)
         return d
 
-    def step(self):
+    def batch(self):
+        """This step's training points and exact targets."""
+        if self.pool_points:
+            st = synth.Stream(self.sample_seed + 1 + self.step_index, tag=401)
+            idx = torch.from_numpy((st.u64(self.n_points) % np.uint64(self.pool_points)).astype(np.int64))
+            idx = idx.cuda()
+            return self.pool_P[idx], self.pool_d[idx]
         P = torch.from_numpy(synth.training_points(
             self.V, self.F, self.n_points, self.sample_seed + self.step_index)).cuda()
-        d = self.targets(P)
+        return P, self.targets(P)
+
+    def step(self):
+        P, d = self.batch()
         f, g = sdf_query(P, self.blob, self.net)
         l1 = (f - d).abs().mean()
         eik = ((g.norm(dim=1) - 1.0) ** 2).mean()
@@ -73,7 +96,8 @@ class MeshFit:
     def state_dict(self):
         return {"blob": self.blob.detach().cpu(), "opt": self.opt.state_dict(),
                 "sched": self.sched.state_dict(), "step": self.step_index,
-                "sample_seed": self.sample_seed, "eikonal": self.eikonal}
+                "sample_seed": self.sample_seed, "eikonal": self.eikonal,
+                "pool_points": self.pool_points}
 
     def save(self, path):
         torch.save(self.state_dict(), path)
@@ -87,6 +111,8 @@ class MeshFit:
         self.step_index = st["step"]
         self.sample_seed = st["sample_seed"]
         self.eikonal = st["eikonal"]
+        if st.get("pool_points") != self.pool_points:
+            raise ValueError("checkpoint was written with pool_points=%r" % st.get("pool_points"))
 
     def weights(self):
         return self.blob.detach().cpu().numpy()

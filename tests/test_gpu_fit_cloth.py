@@ -39,6 +39,28 @@ def test_fit_reduces_loss_and_resumes_bit_identically(nsdf, tmp_path):
     np.testing.assert_array_equal(other.weights(), a)
 
 
+def test_pool_fit_reduces_loss_and_resumes_bit_identically(nsdf, tmp_path):
+    """The pool mode (points and targets sampled once, seeded batches per step)
+    trains, and a checkpoint resumes bit-identically; a checkpoint of the
+    other mode is refused."""
+    from paper_2110_01614_gb300.fit import MeshFit
+    V, F = synth.displaced_icosphere(level=3, seed=7)
+    fit = MeshFit(TINY, V, F, n_points=20000, lr=2e-3, pool_points=60000)
+    hist, _ = fit.run(40)
+    assert hist[-1][1] < 0.6 * hist[0][1]
+    ck = str(tmp_path / "pool.pt")
+    fit.save(ck)
+    fit.run(5)
+    a = fit.weights().copy()
+    other = MeshFit(TINY, V, F, n_points=20000, lr=2e-3, pool_points=60000)
+    other.load(ck)
+    other.run(5)
+    np.testing.assert_array_equal(other.weights(), a)
+    fresh = MeshFit(TINY, V, F, n_points=20000, lr=2e-3)
+    with pytest.raises(ValueError):
+        fresh.load(ck)
+
+
 def test_fitted_network_matches_mesh_distances(nsdf):
     from paper_2110_01614_gb300.fit import MeshFit
     V, F = synth.displaced_icosphere(level=3, seed=7)
