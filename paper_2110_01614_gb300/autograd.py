@@ -16,6 +16,9 @@ from . import NSDF_RAW_GRADIENT, nsdf_backward, nsdf_query
 class SDFQuery(torch.autograd.Function):
     @staticmethod
     def forward(ctx, pts, blob, net):
+        # an output the loss does not use gets no gradient (None, not zeros),
+        # so a loss of f alone takes the first-order path of nsdf_backward
+        ctx.set_materialize_grads(False)
         net.load(blob.detach())
         out = torch.empty_like(pts)
         nsdf_query(net.ctx, pts, out, NSDF_RAW_GRADIENT)
