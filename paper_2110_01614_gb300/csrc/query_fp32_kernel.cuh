@@ -65,22 +65,29 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// softplus_beta(z) = max(z,0) + log1p(exp(-beta|z|))/beta and its derivative
-// sigmoid(beta z), both from the same exp(-beta|z|).
-__device__ __forceinline__ void softplus_and_slope(float z, float beta, float &h, float &s) {
-  float e = expf(-beta * fabsf(z));
-  h = fmaxf(z, 0.0f) + log1pf(e) / beta;
-  float inv = 1.0f / (1.0f + e);
-  s = (z >= 0.0f) ? inv : e * inv;
+// softplus_beta(z) = max(z,0) + log1p(u)/beta and its derivative
+// sigmoid(beta z), both from the same u = exp(-beta|z|) in (0, 1].  The
+// hardware approximations suffice for the FP32 form: log(1 + u) on [1, 2]
+// carries an absolute error of about 2^-21 and forming 1 + u at most ulp(1)/2,
+// both divided by beta (1e-9 for beta = 100); exp and the reciprocal err by
+// a few ulp relative, which moves u and the slope by about 1e-6 relative.
+__device__ __forceinline__ void softplus_and_slope(float z, float beta, float inv_beta, float &h,
+                                                   float &s) {
+  const float u = __expf(-beta * fabsf(z));
+  const float one_u = 1.0f + u;
+  h = fmaf(__logf(one_u), inv_beta, fmaxf(z, 0.0f));
+  const float inv = __fdividef(1.0f, one_u);
+  s = (z >= 0.0f) ? inv : u * inv;
 }
 
 // The activation (softplus_beta or ReLU) and its slope.
-__device__ __forceinline__ void act_and_slope(float z, float beta, int relu, float &h, float &s) {
+__device__ __forceinline__ void act_and_slope(float z, float beta, float inv_beta, int relu, float &h,
+                                              float &s) {
   if (relu) {
     h = fmaxf(z, 0.0f);
     s = z > 0.0f ? 1.0f : 0.0f;   // no gradient through a ReLU that outputs 0
   } else {
-    softplus_and_slope(z, beta, h, s);
+    softplus_and_slope(z, beta, inv_beta, h, s);
   }
 }
 
@@ -162,6 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
   const int skip = prm.skip;
   const int nshort = W - 3;   // outputs of the layer feeding the skip
   const float beta = prm.beta;
+  const float inv_beta = 1.0f / prm.beta;
   const bool grouped = prm.g_nets > 0;
   const int64_t ntiles = grouped ? (int64_t)prm.g_tile_start[prm.g_nets] : (prm.n + C::P - 1) / C::P;
   // per-CTA slope slab: [L-1][PT][CT][kThreads]
@@ -270,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) query_fp32_kernel(QueryParams prm
 #pragma unroll
         for (int i = 0; i < C::PT; ++i) {
           float h, s;
-          act_and_slope(acc[i][j] + bc, beta, prm.relu, h, s);
+          act_and_slope(acc[i][j] + bc, beta, inv_beta, prm.relu, h, s);
           const int pr = g * C::PT + i;
           if (last) {
             fpart[i] = fmaf(wo, h, fpart[i]);
