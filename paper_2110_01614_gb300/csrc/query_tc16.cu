@@ -32,9 +32,11 @@
 // TMEM owner, warps 2, 3 idle, warps 4..11 = epilogue (warp w reads TMEM
 // lanes 32*(w%4)..+31; of each 256-column half of a layer, warps 4..7 take
 // the first 128 columns, warps 8..11 the last 128).  Producer, MMA and epilogue hand over
-// through mbarriers; every wait is bounded (QueryParams::wait_budget cycles)
-// and on expiry the kernel records kDevTimeout, drains what it has in flight
-// and returns.
+// through mbarriers; every wait sleeps between tests of its barrier (a
+// suspend-time hint, so that the polling of the producer and the MMA issuer
+// does not take issue slots from the epilogue warps beside them) and is
+// bounded (QueryParams::wait_budget cycles): on expiry the kernel records
+// kDevTimeout, drains what it has in flight and returns.
 //
 // Products and epilogues overlap within a tile.  Each product runs as two
 // column halves, half h landing in TMEM columns 256h..256h+255; each half
@@ -263,7 +265,7 @@ struct Gate {
       const uint32_t bar = part ? bar1 : bar0;
       if (part) pending1 = false;
       else pending0 = false;
-      ok = (mbar_try_wait(bar, parity) || mbar_wait(bar, parity, budget, abort)) && ok;
+      ok = (mbar_try_wait<true>(bar, parity) || mbar_wait<true>(bar, parity, budget, abort)) && ok;
       tc_fence_after();
     }
   }
@@ -726,7 +728,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const CUtensorMap *map = fwd ? &tmap_fwd : &tmap_bwd;
           const int rowbase = (l - 1) * kW;
           for (int ld = 0; ld < kLoadsPerLayer; ++ld, ++load_idx) {
-            if (!mbar_wait(empty_bar(stage), phase ^ 1u, budget, abort_flag)) {
+            if (!mbar_wait<true>(empty_bar(stage), phase ^ 1u, budget, abort_flag)) {
               fail();
               ok = false;
               break;
@@ -748,7 +750,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < kStages; ++s) {
         if (issued_mask & (1u << s)) {
           volatile int no_abort = 0;
-          if (!mbar_wait(full_bar(s), (issued_parity >> s) & 1u, budget, &no_abort)) fail();
+          if (!mbar_wait<true>(full_bar(s), (issued_parity >> s) & 1u, budget, &no_abort)) fail();
         }
       }
     }
@@ -766,14 +768,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             // starts, atoms 4, 6 and then 5, 7 (and TMEM half 1 read) later
             if (nh == 0 && (pos == 0 || pos == 4 || pos == 6)) {
               const uint32_t bar = pos == 0 ? a_lo : (pos == 4 ? a_hi_a : a_hi_b);
-              if (!mbar_wait(bar, a_phase, budget, abort_flag)) {
+              if (!mbar_wait<true>(bar, a_phase, budget, abort_flag)) {
                 fail();
                 ok = false;
                 break;
               }
               tc_fence_after();
             }
-            if (!mbar_wait(full_bar(stage), phase, budget, abort_flag)) {
+            if (!mbar_wait<true>(full_bar(stage), phase, budget, abort_flag)) {
               fail();
               ok = false;
               break;
@@ -801,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // drain: no product may still be writing TMEM when it is freed
       mma_commit(mma_done);
       volatile int no_abort = 0;
-      if (!mbar_wait(mma_done, 0, budget, &no_abort)) fail();
+      if (!mbar_wait<true>(mma_done, 0, budget, &no_abort)) fail();
     }
   }
   finish(warp == 1);
@@ -838,7 +840,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // gets the gates it must pass before it overwrites A's columns 0..255
     auto begin_half = [&](int h, Gate &gate) -> bool {
       gate = Gate{lo_free_a, lo_free_b, d_phase, budget, abort_flag, h == 0, h == 0, true};
-      if (!mbar_wait(h == 0 ? d0_full : d1_full, d_phase, budget, abort_flag)) return false;
+      if (!mbar_wait<true>(h == 0 ? d0_full : d1_full, d_phase, budget, abort_flag)) return false;
       tc_fence_after();
       return true;
     };
@@ -922,14 +924,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
       // ---- a7-a9: combine the two column halves, normalise, test, project ----
       if (ch == 1) {
-        if (!mbar_wait(x_empty, x_phase ^ 1u, budget, abort_flag)) { fail(); ok = false; break; }
+        if (!mbar_wait<true>(x_empty, x_phase ^ 1u, budget, abort_flag)) { fail(); ok = false; break; }
         exch[r] = make_float4(gx, gy, gz, fpart);
         __syncwarp();
         if (lane == 0) mbar_arrive(x_full);
         x_phase ^= 1u;
         continue;
       }
-      if (!mbar_wait(x_full, x_phase, budget, abort_flag)) { fail(); ok = false; break; }
+      if (!mbar_wait<true>(x_full, x_phase, budget, abort_flag)) { fail(); ok = false; break; }
       x_phase ^= 1u;
       const float4 o = exch[r];
       __syncwarp();

@@ -28,23 +28,46 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
                : "memory");
 }
+// Suspend-time hint of the sleeping waits: a thread whose phase has not
+// completed is suspended (for at most this long, and woken when the phase
+// completes) instead of polling again, leaving the issue slots of its
+// sub-partition to the warps that work.
+constexpr uint32_t kWaitSleepNs = 20000;
+
+// One test of the phase of the given parity; kSleep adds the suspend-time
+// hint.  The width-512 kernel sleeps in every wait: there the polling of the
+// TMA producer and the MMA issuer competed with the epilogue warps of their
+// sub-partitions (1M-point launch 7.43 -> 7.26 ms).  The Fourier-feature
+// kernel polls: its products wait on short hand-overs (1.81 ms polling,
+// 1.86 ms with every wait sleeping).
+template <bool kSleep = false>
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
+  if constexpr (kSleep) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(kWaitSleepNs)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  }
   return ok != 0;
 }
 // Wait for the phase of the given parity; false once `budget` clock cycles
 // have passed or another role has raised the abort flag.
+template <bool kSleep = false>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget,
                                           volatile int *abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait<kSleep>(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
+  while (!mbar_try_wait<kSleep>(bar, parity)) {
     if (*abort_flag) return false;
     if (clock64() - t0 > budget) return false;
   }
