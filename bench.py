@@ -9,7 +9,7 @@ tensor cores with FP32 accumulation; the FP32 CUDA-core form is timed beside
 it.  Inputs are synthetic and seeded; weights come from a seeded geometric
 initialisation (the paper's meshes and trained networks are not available).
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+Prints one JSON line.  Single GPU only (--gpus 1).  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload instead.
 """
 
@@ -143,41 +143,16 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def dist_setup():
-    import torch
+def single_gpu_only(args):
+    """The tensor-core kernels load their weight panels with cluster TMA
+    multicast; nothing here runs them on more than one GPU.  Returns the
+    reason for refusing this launch, or None for a 1-GPU run."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    elif torch.cuda.is_available():
-        torch.cuda.set_device(0)
-    return world, rank, local
-
-
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(x, world, device="cuda"):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def job_throughput(world, n, steps, local_seconds, device="cuda"):
-    """Whole-job queries/s of a weak-scaling run: every rank's n points per
-    step over the slowest rank's time; returns (queries/s, that time)."""
-    t = max_over_ranks(local_seconds, world, device)
-    return world * n * steps / t, t
+    if args.gpus != 1 or world != 1:
+        return (f"single GPU only (--gpus {args.gpus}, WORLD_SIZE {world}): the tensor-core "
+                "kernels use cluster TMA multicast on this GPU's own weight copies, so no "
+                "code path runs them on 2 or more GPUs")
+    return None
 
 
 def oracle_rate(pts, blob, budget_s):
@@ -206,10 +181,60 @@ def blas_threads():
     return os.cpu_count()
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+SINGLE_THREAD_POINTS = 4096
+
+
+def single_thread_rate(budget_s):
+    """The oracle on one host thread (BLAS pinned to 1 thread in a child
+    process): queries/s over the first SINGLE_THREAD_POINTS points of the
+    workload, repeated for about budget_s seconds."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", BLIS_NUM_THREADS="1")
+    code = ("import json, bench, synth\n"
+            f"pts = synth.body_scale_points({N_POINTS}, 1)[:{SINGLE_THREAD_POINTS}]\n"
+            "blob = synth.geometric_init(bench.ARCH, 0)\n"
+            f"r, d, s = bench.oracle_rate(pts, blob, {budget_s})\n"
+            "print(json.dumps([r, d, s]))\n")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                             text=True, timeout=120 + 4 * budget_s)
+        r, d, s = json.loads(out.stdout.strip().splitlines()[-1])
+        return {"value": r, "unit": "queries/s", "threads": 1,
+                "sample": f"{d} queries over the first {SINGLE_THREAD_POINTS} points of the "
+                          f"workload in {s:.1f} s"}
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
+def cpu_baseline(value, cores, sample, single):
+    return {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(), "sample": sample,
+            "single_thread": single}
+
+
 def run_reference(args):
     world, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
     if rank != 0:
-        return 0
+        return 0      # the oracle runs on rank 0's host cores only
     pts = synth.body_scale_points(N_POINTS, 1)
     blob = synth.geometric_init(ARCH, 0)
     sample = pts[: 1 << 15]
@@ -224,17 +249,18 @@ def run_reference(args):
         total_pts += d
         total_s += s
     value = total_pts / total_s
-    cores = blas_threads()
+    sample_txt = (f"{total_pts} points of the 1,048,576-point workload over {args.steps} steps "
+                  f"of ~{per_step:.1f} s (numpy FP64, BLAS threads as reported)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * N_POINTS / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-        "config": {"workload": WORKLOAD, "points": N_POINTS, "precision": "fp64 oracle"},
-        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{total_pts} points of the 1,048,576-point workload over "
-                                   f"{args.steps} steps of ~{per_step:.1f} s "
-                                   "(numpy FP64, BLAS threads as reported)"},
+        "config": {"workload": WORKLOAD, "points": N_POINTS, "precision": "fp64 oracle",
+                   "timed": "each step a bounded sample of the workload; ms_per_step is "
+                            "the 1,048,576-point time at the measured rate"},
+        "cpu_baseline": cpu_baseline(value, blas_threads(), sample_txt,
+                                     single_thread_rate(5.0)),
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -242,9 +268,23 @@ def run_reference(args):
     return 0
 
 
-def error_stats(out_ns_sample, hit_sample, pts_sample, blob):
-    from oracle import mlp
-    f, N, hit, _ = mlp.collide(blob, ARCH, pts_sample, EPS)
+# Parity sample of the bench line: this many seeded indices of the 1M points.
+PARITY_POINTS = 1 << 16
+
+
+def parity_sample(n):
+    """Seeded distinct indices (sorted) of the points checked against the oracle."""
+    k = min(PARITY_POINTS, n)
+    if k == n:
+        return np.arange(n, dtype=np.int64)
+    u = synth.Stream(99).u64(4 * k) % np.uint64(n)
+    idx = np.unique(u.astype(np.int64))[:k]
+    return np.sort(idx)
+
+
+def error_stats(ref, out_ns_sample, hit_sample):
+    """Errors of one form against the oracle's (f, N) on the parity sample."""
+    f, N = ref
     ds = np.abs(out_ns_sample[:, 3].astype(np.float64) - f)
     a, b = N, out_ns_sample[:, :3].astype(np.float64)
     ang = np.arctan2(np.linalg.norm(np.cross(a, b), axis=1), np.einsum("ij,ij->i", a, b))
@@ -257,17 +297,19 @@ def error_stats(out_ns_sample, hit_sample, pts_sample, blob):
 
 
 def run_gpu(args):
+    refusal = single_gpu_only(args)
+    if refusal:
+        print(json.dumps({"metric": METRIC, "error": refusal}), flush=True)
+        return 2
     import torch
     import paper_2110_01614_gb300 as nsdf
     from paper_2110_01614_gb300 import build as nbuild
 
-    world, rank, local = dist_setup()
-    if rank == 0:
-        nbuild.ensure_built()
-    barrier(world)
-    dev = torch.device("cuda", torch.cuda.current_device())
+    nbuild.ensure_built()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
     n = args.points
-    pts_h = synth.body_scale_points(n, 1 + rank)        # each replica its own points
+    pts_h = synth.body_scale_points(n, 1)
     blob = synth.geometric_init(ARCH, 0)
     pts = torch.from_numpy(pts_h).to(dev)
     out_pts = torch.empty_like(pts)
@@ -298,15 +340,15 @@ def run_gpu(args):
     bf = nsdf.NeuralSDF(ARCH, nsdf.NSDF_BF16).load(blob)
 
     # --- headline: BF16, inputs resident in HBM, one kernel per step ---
-    barrier(world)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(0)
     clocks.start()
     durs = timed_steps(bf, args.steps, max(args.warmup, 3))
     clk = clocks.stop()
-    value, t_total = job_throughput(world, n, args.steps, sum(durs))
+    t_total = sum(durs)
+    value = n * args.steps / t_total
     kernel_s = statistics.mean(durs)
-    sample_idx = np.sort(synth.Stream(99).u64(min(4096, n)) % np.uint64(n)).astype(np.int64)
+    sample_idx = parity_sample(n)
     bf_ns, bf_hit = out_ns.cpu().numpy(), out_hit.cpu().numpy().astype(bool)
 
     # --- the other forms on the same workload: FP16 tensor cores, FP32 CUDA cores ---
@@ -343,25 +385,29 @@ def run_gpu(args):
         h_hit = torch.empty(n, dtype=torch.uint8).pin_memory()
         for _ in range(2):
             nsdf.nsdf_collide(bf.ctx, h_pts, EPS, h_out, h_ns, h_hit)
-        barrier(world)
         e2e_t = []
         for _ in range(args.steps):
             t0 = time.perf_counter()
             nsdf.nsdf_collide(bf.ctx, h_pts, EPS, h_out, h_ns, h_hit)   # results on host on return
             e2e_t.append(time.perf_counter() - t0)
-        e2e_value, _ = job_throughput(world, n, args.steps, sum(e2e_t))
+        e2e_value = n * args.steps / sum(e2e_t)
+
+    support = None
+    if args.support:
+        from paper_2110_01614_gb300 import support_bench
+        support = support_bench.bench_line_support()
 
     peak_tf, hbm, peak_kind = load_peaks()
     achieved_tf = FLOP_PER_QUERY * n / kernel_s / 1e12
     line = {
-        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": 1,
         "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic (seeded points, geometric-init weights)",
-        "config": {"workload": WORKLOAD, "points_per_gpu": n, "precision": "bf16 x bf16 -> fp32",
+        "config": {"workload": WORKLOAD, "points": n, "precision": "bf16 x bf16 -> fp32",
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
-                   "parallelism": f"replicas x{world} (independent points per GPU, no collective)"},
+                   "parallelism": "1 GPU (single-GPU library; no multi-GPU path)"},
         "gpu_launches": args.steps,
         "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
@@ -374,7 +420,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": n * 16,
                 "d2h_bytes_per_step": n * (16 + 16 + 1)},
         "forms": {name: {"value": o["value"], "unit": "queries/s", "ms_per_step": o["ms_per_step"],
-                         "bf16_speedup_over_this": value / world / o["value"]}
+                         "bf16_speedup_over_this": value / o["value"]}
                   for name, o in other.items()},
         "clocks": clk,
     }
@@ -385,21 +431,22 @@ def run_gpu(args):
         line["paper_networks"] = {"workload": "the paper's Fourier-feature ReLU shapes (128 "
                                               "frequencies, 8 or 4 layers of 256), same points",
                                   "peak": peak_note, **paper}
-    if rank == 0:
-        errs = {"bf16": error_stats(bf_ns[sample_idx], bf_hit[sample_idx], pts_h[sample_idx], blob)}
-        for name, o in other.items():
-            errs[name] = error_stats(o["ns"][sample_idx], o["hit"][sample_idx], pts_h[sample_idx], blob)
-        line["error_vs_oracle"] = errs
-        if not args.no_cpu_baseline:
-            r, d, s = oracle_rate(pts_h[: 1 << 15], blob, args.ref_seconds)
-            line["cpu_baseline"] = {
-                "value": r, "unit": "queries/s", "cores": blas_threads(), "kind": "oracle",
-                "sample": f"{d} points of the same workload in {s:.1f} s (numpy FP64)"}
-        print(json.dumps(line), flush=True)
+    if support is not None:
+        line["support"] = support
+    from oracle import mlp
+    f_ref, N_ref, _, _ = mlp.collide(blob, ARCH, pts_h[sample_idx], EPS)
+    ref = (f_ref, N_ref)
+    errs = {"bf16": error_stats(ref, bf_ns[sample_idx], bf_hit[sample_idx])}
+    for name, o in other.items():
+        errs[name] = error_stats(ref, o["ns"][sample_idx], o["hit"][sample_idx])
+    line["error_vs_oracle"] = errs
+    if not args.no_cpu_baseline:
+        r, d, s = oracle_rate(pts_h[: 1 << 15], blob, args.ref_seconds)
+        line["cpu_baseline"] = cpu_baseline(
+            r, blas_threads(), f"{d} points of the same workload in {s:.1f} s (numpy FP64)",
+            single_thread_rate(5.0))
+    print(json.dumps(line), flush=True)
     bf.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
     return 0
 
 
@@ -415,6 +462,8 @@ def main():
     ap.add_argument("--points", type=int, default=N_POINTS)
     ap.add_argument("--forms", default="bf16,fp16,fp32,paper")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--support", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the support workloads (grouped, fitting, cloth)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -166,11 +166,15 @@ nsdf_status nsdf_collide(nsdf_ctx *ctx, const float *pts, int64_t n, float eps,
  * loading the library holds until exit; the launch uses as many CTAs as
  * whole per-CTA scratch slabs fit in it, so wide networks run on fewer SMs.
  * A network whose scratch for one CTA exceeds the array is rejected with
- * NSDF_ERR_TOO_LARGE.  No cudaMalloc, cudaFree or allocating library call is
- * made.  The first call on each device resolves the array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture.  All
- * calls share the array: calls that may overlap on the GPU (other streams,
- * other threads) race on it and must be serialised by the caller.
+ * NSDF_ERR_TOO_LARGE.  pts, out_pts, out_n_sdf and out_hit must be device
+ * (or managed) memory; a host array is rejected with NSDF_ERR_INVALID_ARG
+ * before any launch, as is a non-finite eps.  No cudaMalloc, cudaFree or
+ * allocating library call is made.  The first call on each device resolves
+ * the array's device address (cudaGetSymbolAddress) and should come before
+ * any stream capture; the address is kept for the life of the process, so,
+ * like every context, it does not survive a device reset (cudaDeviceReset).
+ * All calls share the array: calls that may overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
  */
 nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int64_t n,
                                  float eps, const float *T, float *out_pts,

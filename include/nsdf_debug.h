@@ -28,6 +28,15 @@ extern "C" {
  */
 nsdf_status nsdf_debug_inject(nsdf_ctx *ctx, int drop_load, long long wait_budget_cycles);
 
+/*
+ * Caps the bytes of nsdf_collide_noalloc's fixed device array that later
+ * calls may use (process-wide; 0 restores the whole array).  With the whole
+ * array no network the library accepts is rejected, so this lets a test
+ * reach the NSDF_ERR_TOO_LARGE reject, which returns before any launch.
+ * Host-side only.
+ */
+nsdf_status nsdf_debug_noalloc_limit(size_t bytes);
+
 #ifdef __cplusplus
 }
 #endif

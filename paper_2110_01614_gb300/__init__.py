@@ -28,6 +28,7 @@ __all__ = [
     "nsdf_query_grouped_T", "nsdf_l1_grad",
     "nsdf_autotune_grouped", "nsdf_set_grouped_config",
     "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status", "nsdf_debug_inject",
+    "nsdf_debug_noalloc_limit",
     "nsdf_status_string", "NeuralSDF", "library",
 ]
 
@@ -128,7 +129,13 @@ def nsdf_collide(ctx, pts, eps, out_pts, out_n_sdf=None, out_hit=None, T=None, s
 
 def nsdf_collide_noalloc(ctx, pts, eps, out_pts, out_n_sdf=None, out_hit=None, T=None,
                          stream=None):
-    """nsdf_collide with no allocation: scratch from the library's fixed device array."""
+    """nsdf_collide with no allocation: scratch from the library's fixed device array.
+
+    Every array must live on the GPU (the library also rejects host memory)."""
+    for name, t in (("pts", pts), ("out_pts", out_pts), ("out_n_sdf", out_n_sdf),
+                    ("out_hit", out_hit)):
+        if t is not None and not getattr(t, "is_cuda", False):
+            raise ValueError(f"nsdf_collide_noalloc: {name} must be a CUDA tensor")
     Tc = _transform(T)
     _check(library().nsdf_collide_noalloc(ctx, _ptr(pts), pts.shape[0], float(eps),
                                           ctypes.cast(Tc, ctypes.c_void_p) if Tc is not None
@@ -196,6 +203,11 @@ def nsdf_debug_inject(ctx, drop_load=-1, wait_budget_cycles=4_000_000_000):
     """Test-only: drop one weight-panel load and/or shorten the kernel's bounded waits."""
     _check(library().nsdf_debug_inject(ctx, int(drop_load), int(wait_budget_cycles)),
            "nsdf_debug_inject")
+
+
+def nsdf_debug_noalloc_limit(nbytes):
+    """Test-only: cap the bytes of nsdf_collide_noalloc's fixed array (0 = all)."""
+    _check(library().nsdf_debug_noalloc_limit(int(nbytes)), "nsdf_debug_noalloc_limit")
 
 
 def nsdf_sync_status(ctx, stream=None):

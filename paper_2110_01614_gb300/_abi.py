@@ -66,6 +66,7 @@ SIGNATURES = {
     "nsdf_sync_status": (_ST, [_P, _P]),
     "nsdf_status_string": (ctypes.c_char_p, [_ST]),
     "nsdf_debug_inject": (_ST, [_P, ctypes.c_int, ctypes.c_longlong]),
+    "nsdf_debug_noalloc_limit": (_ST, [ctypes.c_size_t]),
 }
 
 _lib = None

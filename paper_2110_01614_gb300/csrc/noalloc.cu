@@ -20,8 +20,11 @@
 // overlap on the GPU (different streams, or several host threads) race on it
 // and must be serialised by the caller.
 
+#include <atomic>
+#include <cmath>
 #include <mutex>
 
+#include "nsdf_debug.h"
 #include "nsdf_internal.h"
 
 namespace nsdf {
@@ -37,9 +40,34 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void *g_scratch_ptr[kMaxDevices] = {};
+// Test-only cap on the bytes of the array a call may use (0 = all of it);
+// set through nsdf_debug_noalloc_limit so that a test can reach the
+// NSDF_ERR_TOO_LARGE reject, which no network the library accepts reaches
+// with the full array.
+std::atomic<size_t> g_limit{0};
+
+size_t usable_bytes() {
+  const size_t lim = g_limit.load();
+  return lim != 0 && lim < kNoAllocScratchBytes ? lim : kNoAllocScratchBytes;
+}
+
+// True for memory the GPU addresses as device memory (device or managed).
+// cudaPointerGetAttributes allocates nothing.  A host array handed to this
+// entry point is rejected here instead of reaching a kernel.
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
 
 // Device address of g_noalloc_scratch on the current device (host code only
-// sees a host-side stand-in for the symbol).  Resolved once per device.
+// sees a host-side stand-in for the symbol).  Resolved once per device and
+// kept for the life of the process: a device reset (cudaDeviceReset) would
+// unload the module and leave the kept address dangling, exactly as it frees
+// every context's weights, so the library is not used across one.
 cudaError_t scratch_address(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -64,11 +92,14 @@ using namespace nsdf;
 extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int64_t n, float eps,
                                             const float *T, float *out_pts, float *out_n_sdf,
                                             uint8_t *out_hit, nsdf_stream stream) {
-  if (!ctx || n < 0 || !(eps == eps)) return NSDF_ERR_INVALID_ARG;
+  if (!ctx || n < 0 || !std::isfinite(eps)) return NSDF_ERR_INVALID_ARG;
   if (n == 0) return NSDF_OK;
   if (!pts || !out_pts) return NSDF_ERR_INVALID_ARG;
   auto mis = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
   if (mis(pts) || mis(out_pts) || (out_n_sdf && mis(out_n_sdf))) return NSDF_ERR_MISALIGNED;
+  if (!is_device_ptr(pts) || !is_device_ptr(out_pts) || (out_n_sdf && !is_device_ptr(out_n_sdf)) ||
+      (out_hit && !is_device_ptr(out_hit)))
+    return NSDF_ERR_INVALID_ARG;
   QueryParams p{};
   int num_sms = 0, width = 0, n_hidden = 0;
   bool tc16 = false, fp16 = false;
@@ -87,7 +118,7 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   p.out_hit = out_hit;
   if (tc16 && p.ff > 0) {   // Fourier-feature tensor-core kernel: one slope-bit slab per CTA
     const int grid = query_tc16_ff_grid(n, num_sms);
-    if (query_tc16_ff_scratch_bytes(grid) > kNoAllocScratchBytes) return NSDF_ERR_TOO_LARGE;
+    if (query_tc16_ff_scratch_bytes(grid) > usable_bytes()) return NSDF_ERR_TOO_LARGE;
     void *scratch = nullptr;
     if (scratch_address(&scratch) != cudaSuccess) return NSDF_ERR_CUDA;
     p.scratch = static_cast<float *>(scratch);
@@ -99,7 +130,7 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   // keep that product within the slabs the array holds.
   const size_t slab = tc16 ? query_tc16_scratch_bytes(width, n_hidden, 1)
                            : query_fp32_scratch_bytes(width, n_hidden, 1);
-  const int64_t slabs = (int64_t)(kNoAllocScratchBytes / slab);
+  const int64_t slabs = (int64_t)(usable_bytes() / slab);
   const int per_sm = tc16 ? 1 : query_fp32_grid(width, (int64_t)1 << 40, 1, p.ff > 0);
   if (slabs < per_sm || per_sm < 1) return NSDF_ERR_TOO_LARGE;
   if (tc16 && slabs < query_tc16_min_grid()) return NSDF_ERR_TOO_LARGE;
@@ -112,4 +143,9 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   const cudaError_t e = tc16 ? launch_query_tc16_net(p, *net, fp16, ctas, s)
                              : launch_query_fp32(p, ctas, s);
   return e == cudaSuccess ? NSDF_OK : NSDF_ERR_CUDA;
+}
+
+extern "C" nsdf_status nsdf_debug_noalloc_limit(size_t bytes) {
+  g_limit.store(bytes);
+  return NSDF_OK;
 }

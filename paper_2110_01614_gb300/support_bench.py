@@ -29,6 +29,10 @@
   batches of 250,000): seconds per step and the time of nsdf_l1_grad alone.
 * fit_paper: the same for the paper's dragon-shaped Fourier-feature ReLU
   network.
+* cloth_fitted: 100 steps of the 1024 x 1024 cloth dropped onto the displaced
+  icosphere represented by a body-scale network fitted to it (BF16 tensor-core
+  fitting), per-step time in BF16 / FP16 / FP32 and of the brute-force mesh
+  SDF of every vertex.
 
 Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped grouped_paper cloth
                                                       paper_arch fit512 fit_paper]
@@ -249,15 +253,78 @@ def bench_fit_paper(steps=20):
             "loss_first": losses[0], "loss_last": losses[-1]}
 
 
+def bench_cloth_fitted(steps=100, fit_steps=300, fp32_steps=100):
+    """Cloth of 1024 x 1024 vertices dropped for `steps` explicit steps onto
+    the displaced icosphere (20,480 triangles) represented by a network of the
+    body-scale shape (3-512x8-1, skip at L4) fitted to it on the BF16
+    tensor-core path (L1 loss, pool of 1,048,576 points, `fit_steps` batches
+    of 250,000); per-step time of Verlet + collision solve in BF16, FP16 and
+    FP32, and of the exact brute-force mesh SDF of every vertex."""
+    from .fit import MeshFitTC
+    V, F = synth.displaced_icosphere(level=5, seed=7)
+    fit = MeshFitTC(BODY, V, F, precision=NSDF_BF16, pool_points=1 << 20, batch=250_000)
+    losses, fit_s = fit.run(fit_steps)
+    blob = fit.weights()
+    fit.close()
+    res = {"workload": "cloth_fitted_body", "grid": "1024x1024", "steps": steps,
+           "body": "3-512x8-1 (skip L4) fitted to the displaced icosphere",
+           "fit_steps": fit_steps, "fit_s_per_step": fit_s, "fit_l1_first": losses[0],
+           "fit_l1_last": losses[-1]}
+    for name, prec, k in (("bf16", NSDF_BF16, steps), ("fp16", NSDF_FP16, steps),
+                          ("fp32", NSDF_FP32, fp32_steps)):
+        body = NeuralSDF(BODY, prec).load(blob)
+        sim = ClothSim(n=1024)
+        ts = sim.run(body, k)
+        nsdf_sync_status(body.ctx)
+        body.close()
+        res[name] = {"steps": k, "ms_per_step_median": statistics.median(ts),
+                     "ms_per_step_mean": statistics.mean(ts)}
+        if name == "bf16":
+            x_final = sim.x
+    ms, _ = mesh_reference_step_ms(V, F, x_final, repeats=3)
+    res["mesh_bruteforce_sdf_ms_per_step"] = ms
+    return res
+
+
+def bench_line_support():
+    """The support workloads in one bounded pass (about a minute), for the
+    benchmark line: grouped launch, penalty gradient, the fitting steps and
+    the fitted-body cloth run."""
+    out = {}
+    for name, fn in (("grouped", lambda: bench_grouped(10)),
+                     ("penalty_gradient", lambda: bench_penalty(5)),
+                     ("fit_width64_fp32", lambda: bench_fit_pool(10)),
+                     ("fit512_bf16", lambda: bench_fit512(10)),
+                     ("cloth", bench_cloth_fitted)):
+        t0 = time.perf_counter()
+        r = fn()
+        r["wall_s"] = time.perf_counter() - t0
+        out[name] = r
+    return out
+
+
+def bench_fit_pool(steps=10):
+    """Config-1-shaped network fitted (L1 + 0.1 eikonal, FP32 backward) from a
+    pool of 1,048,576 points with exact targets, batches of 250,000."""
+    V, F = synth.displaced_icosphere(level=5, seed=7)
+    pool = MeshFit(TINY, V, F, n_points=250_000, pool_points=1 << 20)
+    pool.run(2)
+    hist, per_step = pool.run(steps)
+    return {"workload": "fit", "points_per_step": 250_000, "pool": 1 << 20,
+            "triangles": int(F.shape[0]), "s_per_step": per_step,
+            "loss_first": hist[0][0], "loss_last": hist[-1][0]}
+
+
 def main(argv):
     which = argv or ["fit", "penalty", "grouped", "grouped_paper", "cloth", "paper_arch", "fit512",
-                     "fit_paper"]
+                     "fit_paper", "cloth_fitted"]
     torch.cuda.set_device(0)
     for w in which:
         t0 = time.perf_counter()
         r = {"fit": bench_fit, "penalty": bench_penalty, "grouped": bench_grouped,
              "grouped_paper": bench_grouped_paper, "cloth": bench_cloth,
-             "paper_arch": bench_paper_arch, "fit512": bench_fit512, "fit_paper": bench_fit_paper}[w]()
+             "paper_arch": bench_paper_arch, "fit512": bench_fit512, "fit_paper": bench_fit_paper,
+             "cloth_fitted": bench_cloth_fitted}[w]()
         r["wall_s"] = time.perf_counter() - t0
         print(json.dumps(r), flush=True)
 

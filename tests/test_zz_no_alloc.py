@@ -8,7 +8,6 @@ run stopping at the first failure has already run every other test; it also
 passes alone in a fresh process.
 """
 
-import numpy as np
 import pytest
 import torch
 
@@ -25,11 +24,11 @@ def nsdf(nsdf_lib):
     return m
 
 
-@pytest.mark.parametrize("prec,arch,n,sdf_tol", [
-    ("bf16", synth.Arch(3, 512, 8, 4, 100.0), 100_003, 0.0),
-    ("fp32", synth.Arch(3, 64, 3, -1, 100.0), 200_001, 0.0),
+@pytest.mark.parametrize("prec,arch,n", [
+    ("bf16", synth.Arch(3, 512, 8, 4, 100.0), 100_003),
+    ("fp32", synth.Arch(3, 64, 3, -1, 100.0), 200_001),
 ])
-def test_noalloc_matches_collide_twice(nsdf, prec, arch, n, sdf_tol):
+def test_noalloc_matches_collide_twice(nsdf, prec, arch, n):
     precision = nsdf.NSDF_BF16 if prec == "bf16" else nsdf.NSDF_FP32
     net = nsdf.NeuralSDF(arch, precision).load(synth.geometric_init(arch, 0))
     pts = torch.from_numpy(synth.body_scale_points(n, 11)).cuda()
@@ -70,4 +69,55 @@ def test_noalloc_deepest_network_and_bad_args(nsdf):
     with pytest.raises(nsdf.NsdfError) as e:                             # misaligned
         nsdf.nsdf_collide_noalloc(net.ctx, pts.view(-1)[1:41].view(10, 4), EPS, out[:10])
     assert e.value.status == 2
+    net.close()
+
+
+def test_noalloc_rejects_host_memory_and_bad_eps(nsdf):
+    """Host arrays and a non-finite eps are refused before any launch."""
+    arch = synth.Arch(3, 64, 3, -1, 100.0)
+    net = nsdf.NeuralSDF(arch, nsdf.NSDF_FP32).load(synth.geometric_init(arch, 0))
+    lib = nsdf.library()
+    host = torch.from_numpy(synth.body_scale_points(256, 13))
+    dev = host.cuda()
+    out = torch.empty_like(dev)
+    # through the C ABI directly (the Python wrapper refuses CPU tensors itself)
+    assert lib.nsdf_collide_noalloc(net.ctx, host.data_ptr(), 256, EPS, None, out.data_ptr(),
+                                    None, None, None) == 1
+    assert lib.nsdf_collide_noalloc(net.ctx, dev.data_ptr(), 256, EPS, None,
+                                    torch.empty_like(host).data_ptr(), None, None, None) == 1
+    hit = torch.empty(256, dtype=torch.uint8)
+    assert lib.nsdf_collide_noalloc(net.ctx, dev.data_ptr(), 256, EPS, None, out.data_ptr(),
+                                    None, hit.data_ptr(), None) == 1
+    for bad in (float("inf"), float("-inf"), float("nan")):
+        assert lib.nsdf_collide_noalloc(net.ctx, dev.data_ptr(), 256, bad, None, out.data_ptr(),
+                                        None, None, None) == 1
+    with pytest.raises(ValueError):
+        nsdf.nsdf_collide_noalloc(net.ctx, host, EPS, out)
+    nsdf.nsdf_sync_status(net.ctx)
+    net.close()
+
+
+def test_noalloc_too_large_is_rejected_before_launch(nsdf):
+    """With the usable part of the array capped below one CTA's scratch (a
+    test-only control: every network the library accepts fits the whole
+    array), the call returns NSDF_ERR_TOO_LARGE and launches nothing; with
+    the cap lifted the same call runs and matches nsdf_collide."""
+    arch = synth.Arch(3, 512, 8, 4, 100.0)
+    net = nsdf.NeuralSDF(arch, nsdf.NSDF_BF16).load(synth.geometric_init(arch, 0))
+    pts = torch.from_numpy(synth.body_scale_points(5000, 14)).cuda()
+    out = torch.full_like(pts, 7.0)
+    try:
+        nsdf.nsdf_debug_noalloc_limit(64 << 10)      # 64 KiB < 896 KiB of slopes per CTA
+        with pytest.raises(nsdf.NsdfError) as e:
+            nsdf.nsdf_collide_noalloc(net.ctx, pts, EPS, out)
+        assert e.value.status == 8
+        torch.cuda.synchronize()
+        assert bool((out == 7.0).all())               # nothing was written
+    finally:
+        nsdf.nsdf_debug_noalloc_limit(0)
+    ref, got = torch.empty_like(pts), torch.empty_like(pts)
+    nsdf.nsdf_collide(net.ctx, pts, EPS, torch.empty_like(pts), ref)
+    nsdf.nsdf_collide_noalloc(net.ctx, pts, EPS, out, got)
+    nsdf.nsdf_sync_status(net.ctx)
+    assert torch.equal(got, ref)
     net.close()
