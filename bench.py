@@ -277,9 +277,9 @@ def parity_sample(n):
     k = min(PARITY_POINTS, n)
     if k == n:
         return np.arange(n, dtype=np.int64)
-    u = synth.Stream(99).u64(4 * k) % np.uint64(n)
-    idx = np.unique(u.astype(np.int64))[:k]
-    return np.sort(idx)
+    u = (synth.Stream(99).u64(4 * k) % np.uint64(n)).astype(np.int64)
+    _, first = np.unique(u, return_index=True)       # distinct draws, in draw order
+    return np.sort(u[np.sort(first)][:k])
 
 
 def error_stats(ref, out_ns_sample, hit_sample):

@@ -229,7 +229,8 @@ int query_grid(const nsdf_ctx *ctx, int64_t n) {
 
 size_t query_scratch(const nsdf_ctx *ctx, int grid) {
   if (use_tc16_ff(ctx)) return query_tc16_ff_scratch_bytes(grid);
-  if (use_bf16(ctx)) return query_tc16_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
+  if (use_bf16(ctx))
+    return query_tc16_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid, ctx->prec == NSDF_FP16);
   return query_fp32_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid);
 }
 

@@ -128,7 +128,7 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   // one slab per CTA; as many CTAs as whole slabs fit.  The launchers size
   // their grid as min(tiles, sm_arg * CTAs per SM), so sm_arg is chosen to
   // keep that product within the slabs the array holds.
-  const size_t slab = tc16 ? query_tc16_scratch_bytes(width, n_hidden, 1)
+  const size_t slab = tc16 ? query_tc16_scratch_bytes(width, n_hidden, 1, fp16)
                            : query_fp32_scratch_bytes(width, n_hidden, 1);
   const int64_t slabs = (int64_t)(usable_bytes() / slab);
   const int per_sm = tc16 ? 1 : query_fp32_grid(width, (int64_t)1 << 40, 1, p.ff > 0);

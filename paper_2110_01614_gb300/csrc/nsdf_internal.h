@@ -117,7 +117,7 @@ bool query_tc16_supported(int width, int n_hidden, int skip);
 bool make_tc16_tmaps(NetDevice &net, int width, int n_hidden, bool fp16);
 cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bool fp16,
                                   int num_sms, cudaStream_t s);
-size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid);
+size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid, bool fp16);
 int query_tc16_grid(int width, int64_t n, int num_sms);
 int query_tc16_min_grid();   // CTAs of one cluster: the smallest grid of the kernel
 

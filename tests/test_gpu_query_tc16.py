@@ -1,16 +1,15 @@
 """GPU parity of the 16-bit tensor-core (tcgen05/TMEM/TMA) fused query vs the FP64 oracle.
 
-Target tolerances: |delta sdf| <= 2e-3 and normal angle <= 1e-2 rad for every
-point, and >= 99.9% agreement of the collision decision f < eps on points
-with |f| > 1e-2.
+Target tolerances, both forms: |delta sdf| <= 2e-3 and normal angle <= 1e-2
+rad for every point, and >= 99.9% agreement of the collision decision
+f < eps on points with |f| > 1e-2.
 
-* FP16 operands (FP32 accumulate) meet all of them.
-* BF16 operands (FP32 accumulate) meet the angle and decision targets and
-  |delta sdf| <= 2e-3 at the 99th percentile; the largest sdf errors reach
-  ~3e-3 because rounding the 512-wide activations to BF16's 8-bit
-  significand at each of 7 tensor-core layers accumulates (a numpy emulation
-  of exactly these roundings reproduces the GPU errors).  Its per-point
-  bound here is 5e-3.
+* FP16 operands (FP32 accumulate) meet them with the plain kernel.
+* BF16 operands (FP32 accumulate): rounding the 512-wide activations to
+  BF16's 8-bit significand at each of 7 tensor-core layers alone moves f by
+  up to ~3.2e-3 at the tail of the 1M-point workload; the kernel adds the
+  first-order correction sum (df/dA) (A - bf16(A)) from its own
+  Jacobian-transpose chain, which leaves the weight rounding (~1.5e-3).
 """
 
 import numpy as np
@@ -27,7 +26,7 @@ BODY = synth.Arch(3, 512, 8, 4, 100.0)
 ANG_TOL, AGREE = 1e-2, 0.999
 EPS = 0.002
 # per precision: (max |delta sdf|, 99th percentile of |delta sdf|)
-SDF_TOL = {"fp16": (2e-3, 2e-3), "bf16": (5e-3, 2e-3)}
+SDF_TOL = {"fp16": (2e-3, 2e-3), "bf16": (2e-3, 2e-3)}
 
 
 @pytest.fixture(scope="module", params=["bf16", "fp16"])
@@ -158,12 +157,16 @@ def test_bounded_wait_reports_timeout_and_recovers(nsdf, prec, blob):
 
 
 def test_full_size_sampled_parity(nsdf, prec, blob):
-    """1,048,576 body-scale points in the benchmark's launch; oracle on a sample."""
+    """1,048,576 body-scale points in the benchmark's launch; the oracle on a
+    seeded sample of 65,536 distinct points (the benchmark's parity sample)
+    plus the last point."""
     n = 1 << 20
     pts = synth.body_scale_points(n, 1)
     out_pts, out_ns, out_hit = collide_gpu(nsdf, prec, blob, pts)
-    idx = np.sort(synth.Stream(99).u64(4096) % np.uint64(n)).astype(np.int64)
-    idx[-1] = n - 1
+    u = (synth.Stream(99).u64(4 * 65536) % np.uint64(n)).astype(np.int64)
+    _, first = np.unique(u, return_index=True)        # distinct draws, in draw order
+    idx = np.unique(np.append(u[np.sort(first)][:65536], n - 1))
+    assert idx.size >= 65536
     f, N, hit, x = mlp.collide(blob, BODY, pts[idx], EPS)
     check(prec, f, N, hit, x, out_pts[idx], out_ns[idx], out_hit[idx], pts[idx])
     # properties that hold at any size: finite outputs, unit normals, hit <=> f < eps
