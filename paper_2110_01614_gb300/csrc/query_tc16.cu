@@ -12,9 +12,10 @@
 //     2-CTA cluster and multicast into both,
 //   * the epilogue warps read z from TMEM (tcgen05.ld), add the bias (the
 //     biases, W_0, the skip weights on p and w_out sit in shared memory)
-//     and write softplus_beta(z) back as the next A operand, and park
-//     sigmoid(beta z) (the slope the reverse chain needs) in a per-CTA
-//     scratch slab (FP16, lane-contiguous, stored evict-first in L2),
+//     and write softplus_beta(z) back as the next A operand, and park what
+//     the reverse chain needs in a per-CTA scratch slab (FP16,
+//     lane-contiguous, stored evict-first in L2): the slope sigmoid(beta z)
+//     in the FP16 form, the activation itself in the BF16 form (below),
 //   * the skip connection's input columns p/sqrt(2) never pass through the
 //     16-bit operands: their product with W_s is added in FP32 on CUDA
 //     cores, and their gradient is accumulated in FP32 from delta_s,
@@ -30,37 +31,18 @@
 //
 // BF16 operand rounding and its first-order correction.  Rounding the
 // 512-wide activations to BF16's 8-bit significand at each tensor-core layer
-// moves f by up to ~3e-3 on the body-scale network, while weight rounding
+// moves f by up to ~3.2e-3 on the body-scale network, while weight rounding
 // alone moves it by ~1.5e-3.  To first order, the change of f caused by
 // replacing an A operand element a by its rounded value a~ is
 // (df/da) (a - a~), and df/da for every element of every A operand is exactly
 // what the Jacobian-transpose chain forms: the reverse product W_l^T delta_l
-// lands in TMEM as df/dA_{l-1}.  So in the BF16 form the forward epilogue
-// keeps each element's rounding residual r = a - a~ (in FP8 e4m3, scaled by
-// 2^12; for the activations computed in packed FP16 the residual is exact in
-// that format) beside its slope, and the reverse epilogue adds
-// sum (df/dA) r to f.  The FP16 form (3 more significand bits) needs no
-// correction and stores no residuals.
-//
-// Warp roles (384 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
-// TMEM owner, warps 2, 3 idle, warps 4..11 = epilogue (warp w reads TMEM
-// lanes 32*(w%4)..+31; of each 256-column half of a layer, warps 4..7 take
-// the first 128 columns, warps 8..11 the last 128).  Producer, MMA and epilogue hand over
-// through mbarriers; every wait sleeps between tests of its barrier (a
-// suspend-time hint, so that the polling of the producer and the MMA issuer
-// does not take issue slots from the epilogue warps beside them) and is
-// bounded (QueryParams::wait_budget cycles): on expiry the kernel records
-// kDevTimeout, drains what it has in flight and returns.
-//
-// Products and epilogues overlap within a tile.  Each product runs as two
-// column halves, half h landing in TMEM columns 256h..256h+255; each half
-// walks the eight 64-column K atoms of A.  The epilogue of half 0 starts as
-// soon as its products are done and runs while half 1 is multiplied; half 1
-// reads atoms 0, 2 first and then 1, 3, and the epilogue rewrites each of
-// those atoms only once they have been read.  The next layer's half 0 starts
-// on atoms 0..3 while the epilogue of half 1 still runs, takes atoms 4 and 6
-// once the epilogue has written its first two chunks of every row, and
-// atoms 5 and 7 last.
+// lands in TMEM as df/dA_{l-1}.  So the BF16 form parks the activation a
+// itself (FP16) in the scratch slab instead of its slope, rounds it to
+// 8 significant bits by an integer operation on its FP16 encoding that the
+// reverse epilogue repeats bit for bit, and there (1) derives the slope as
+// sigmoid(beta z) = 1 - e^{-beta h} (h = softplus_beta(z)) and (2) adds
+// sum (df/da) (a - a~) to f.  The slab keeps its size; the FP16 form (3 more
+// significand bits) needs no correction and parks its slopes.
 
 #include <cudaTypedefs.h>
 
@@ -108,14 +90,7 @@ static_assert(128 * kCtlRegs + 32 * kEpiWarps * kEpiRegs <= kThreads * kLaunchRe
               "register split exceeds the registers of the launch");
 static_assert(kThreads * kLaunchRegs <= 65536, "launch registers exceed the SM");
 constexpr float kInvSqrt2 = 0.70710678118654752f;
-// Scale of the stored BF16 rounding residuals (FP8 e4m3): |r| <= 2^-9 |a|, so
-// r 2^12 stays in e4m3's normal range for the activations of a layer and
-// saturates only for |a| >= 56.
-constexpr float kResScale = 4096.0f;
-// Bytes of per-CTA scratch per slab element: the FP16 slope, plus the e4m3
-// residual in the BF16 form.
-template <bool kF16>
-constexpr int kSlabElemBytes = kF16 ? 2 : 3;
+constexpr float kSqrt2 = 1.41421356237309515f;
 
 // shared-memory map (bytes from a 1024-aligned base)
 constexpr int kOffA = 0;
@@ -233,6 +208,7 @@ __device__ __forceinline__ __half2 h2_tanh(__half2 x) {
 }
 struct ActH2 {          // per-kernel constants of act_h2
   __half2 neg_bl2e, inv_beta, half_beta;
+  __half2 neg_bl2e_s2;  // -beta log2(e) sqrt(2): slope of the layer feeding the skip
 };
 __device__ __forceinline__ void act_h2(float z0, float z1, const ActH2 &k, __half2 &h, __half2 &s) {
   const __half2 zh = __floats2half2_rn(z0, z1);
@@ -249,32 +225,37 @@ __device__ __forceinline__ void act_h2(float z0, float z1, const ActH2 &k, __hal
 }
 __device__ __forceinline__ uint32_t h2_bits(__half2 v) { return *reinterpret_cast<uint32_t *>(&v); }
 
-// Two FP32 values as FP8 e4m3 (round to nearest, saturating): lo in the low
-// byte, hi in the high byte of the 16-bit result.
-__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
-  uint16_t d;
-  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;\n" : "=h"(d) : "f"(hi), "f"(lo));
-  return d;
-}
-// Two e4m3 bytes (low byte -> low half) as FP16x2.
-__device__ __forceinline__ __half2 e4m3x2_to_h2(uint32_t b) {
-  uint32_t d;
-  const uint16_t s = (uint16_t)b;
-  asm("cvt.rn.f16x2.e4m3x2 %0, %1;\n" : "=r"(d) : "h"(s));
-  return *reinterpret_cast<__half2 *>(&d);
-}
 // Two FP32 values as FP16x2 (lo -> low half), saturating at +-65504.
 __device__ __forceinline__ __half2 h2_sat(float lo, float hi) {
   uint32_t d;
   asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;\n" : "=r"(d) : "f"(hi), "f"(lo));
   return *reinterpret_cast<__half2 *>(&d);
 }
-// Scaled rounding residuals of the BF16 pair w = bf16x2(lo, hi), as two e4m3
-// bytes: (x - bf16(x)) 2^12 for x = lo, hi (the differences are exact).
-__device__ __forceinline__ uint32_t res_pair(float lo, float hi, uint32_t w) {
-  const float rl = (lo - __uint_as_float(w << 16)) * kResScale;
-  const float rh = (hi - __uint_as_float(w & 0xffff0000u)) * kResScale;
-  return e4m3x2(rl, rh);
+// BF16 form: both FP16 values of a pair (non-negative, finite) rounded to
+// 8 significant bits, to nearest even, on their FP16 encoding (the carry of
+// the low half cannot reach the high half for such values).  For normal
+// FP16 values this is the BF16 rounding; the result converts to BF16
+// exactly, and the reverse epilogue recomputes it bit for bit.
+__device__ __forceinline__ uint32_t rnd8_h2(uint32_t x) {
+  return (x + 0x00030003u + ((x >> 3) & 0x00010001u)) & 0xfff8fff8u;
+}
+// The BF16 A word of an FP16 pair already rounded to 8 significant bits (exact).
+__device__ __forceinline__ uint32_t bf16_of_h2(uint32_t a) {
+  const float2 f = __half22float2(*reinterpret_cast<__half2 *>(&a));
+  return pack16<false>(f.x, f.y);
+}
+// softplus_beta of a pair in packed FP16, without its slope (the BF16 form
+// keeps the activation and derives the slope in the reverse epilogue).
+__device__ __forceinline__ __half2 act_h2_h(float z0, float z1, const ActH2 &k) {
+  const __half2 zh = __floats2half2_rn(z0, z1);
+  const __half2 u = h2_ex2(__hmul2(__habs2(zh), k.neg_bl2e));
+  __half2 p = __float2half2_rn(-2.344365580e-02f);
+  p = __hfma2(p, u, __float2half2_rn(1.001397327e-01f));
+  p = __hfma2(p, u, __float2half2_rn(-2.090795360e-01f));
+  p = __hfma2(p, u, __float2half2_rn(3.248495807e-01f));
+  p = __hfma2(p, u, __float2half2_rn(-4.993146523e-01f));
+  p = __hfma2(p, u, __float2half2_rn(9.999905920e-01f));
+  return __hfma2(__hmul2(u, p), k.inv_beta, __hmax2(zh, __float2half2_rn(0.0f)));
 }
 
 // The kernel's dynamic shared memory (same base as the kernel's own view).
@@ -350,22 +331,12 @@ struct Epi {
   // 16-bit arrays, activations h_l to save_h[l], deltas to save_d[l]
   uint16_t *save_h, *save_d;
   int64_t n_pad, row;   // rows of a saved layer; this thread's row in it
-  uint8_t *resb;        // BF16 form: this CTA's residual area (after its slopes)
-  // slopes of layer l, columns 8g..8g+7 (16 B) of this row
+  // slab words of layer l, columns 8g..8g+7 (16 B) of this row: FP16 slopes
+  // (FP16 form) or FP16 activations (BF16 form)
   __device__ __forceinline__ uint4 *slope(int l, int g) const {
     return reinterpret_cast<uint4 *>(slab + (((size_t)l * (kW / 8) + g) * kM + r) * 16);
   }
-  // scaled rounding residuals of A operand l, columns 16g..16g+15 (16 B) of this row
-  __device__ __forceinline__ uint4 *res(int l, int g) const {
-    return reinterpret_cast<uint4 *>(resb + (((size_t)l * (kW / 16) + g) * kM + r) * 16);
-  }
 };
-
-// BF16 form: the 32 residual bytes of a chunk (columns c0..c0+31) of A operand l.
-__device__ __forceinline__ void store_res(const Epi &e, int l, int c0, const uint32_t (&rw)[8]) {
-  st_slope(e.res(l, c0 >> 4), make_uint4(rw[0], rw[1], rw[2], rw[3]), e.pol);
-  st_slope(e.res(l, (c0 >> 4) + 1), make_uint4(rw[4], rw[5], rw[6], rw[7]), e.pol);
-}
 
 constexpr int kNShort = kW - 3;
 
@@ -388,8 +359,7 @@ template <bool kF16, bool LAST, bool AT_SKIP, bool FEEDS_SKIP, bool kSave = fals
 __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uint32_t (&raw)[32],
                                           Acc &acc, uint32_t (&hw)[16], uint32_t (&hx)[16]) {
   const int b = l * kW + c0;     // bias index
-  uint32_t sw[16];
-  uint32_t rw[8];                // BF16 form: scaled rounding residuals of the A words
+  uint32_t sw[16];               // slab words: FP16 slopes (FP16 form) / activations (BF16)
   if constexpr (!LAST && !FEEDS_SKIP) {
     // activations and slopes in packed FP16; slopes are kept as FP16 in the slab
 #pragma unroll
@@ -408,28 +378,25 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
         if (AT_SKIP)
           z[u] = fmaf(kInvSqrt2, fmaf(comp(s0, u), e.px, fmaf(comp(s1, u), e.py, comp(s2, u) * e.pz)), z[u]);
       }
-      uint32_t rp[2];
 #pragma unroll
       for (int v = 0; v < 2; ++v) {
-        __half2 h, sl;
-        act_h2(z[2 * v], z[2 * v + 1], e.kh, h, sl);
-        if (kF16) {
+        if constexpr (kF16) {
+          __half2 h, sl;
+          act_h2(z[2 * v], z[2 * v + 1], e.kh, h, sl);
           hw[2 * q + v] = h2_bits(h);
+          sw[2 * q + v] = h2_bits(sl);
         } else {
-          const float2 hf = __half22float2(h);
-          hw[2 * q + v] = Op<false>::pack(hf.x, hf.y);
-          rp[v] = res_pair(hf.x, hf.y, hw[2 * q + v]);
+          const uint32_t hb = h2_bits(act_h2_h(z[2 * v], z[2 * v + 1], e.kh));
+          hw[2 * q + v] = bf16_of_h2(rnd8_h2(hb));
+          sw[2 * q + v] = hb;
         }
-        sw[2 * q + v] = h2_bits(sl);
       }
-      if constexpr (!kF16) rw[q] = rp[0] | (rp[1] << 16);
     }
     const int g0 = c0 >> 3;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       st_slope(e.slope(l, g0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
                e.pol);
-    if constexpr (!kF16) store_res(e, l, c0, rw);
   } else {
     // the layer feeding the skip connection and the last layer: FP32 activation
 #pragma unroll
@@ -468,12 +435,18 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
           hv[u] = (c < kNShort) ? hv[u] * kInvSqrt2 : 0.0f;
         }
       }
-      hw[2 * q] = Op<kF16>::pack(hv[0], hv[1]);
-      hw[2 * q + 1] = Op<kF16>::pack(hv[2], hv[3]);
-      if constexpr (!kF16 && !LAST)
-        rw[q] = res_pair(hv[0], hv[1], hw[2 * q]) | (res_pair(hv[2], hv[3], hw[2 * q + 1]) << 16);
-      sw[2 * q] = Op<true>::pack(sv[0], sv[1]);
-      sw[2 * q + 1] = Op<true>::pack(sv[2], sv[3]);
+      if constexpr (!kF16 && !LAST) {
+        // BF16 form: the activation as FP16 into the slab, its 8-bit rounding as A
+        sw[2 * q] = h2_bits(__floats2half2_rn(hv[0], hv[1]));
+        sw[2 * q + 1] = h2_bits(__floats2half2_rn(hv[2], hv[3]));
+        hw[2 * q] = bf16_of_h2(rnd8_h2(sw[2 * q]));
+        hw[2 * q + 1] = bf16_of_h2(rnd8_h2(sw[2 * q + 1]));
+      } else {
+        hw[2 * q] = Op<kF16>::pack(hv[0], hv[1]);
+        hw[2 * q + 1] = Op<kF16>::pack(hv[2], hv[3]);
+        sw[2 * q] = Op<true>::pack(sv[0], sv[1]);
+        sw[2 * q + 1] = Op<true>::pack(sv[2], sv[3]);
+      }
     }
     if constexpr (!LAST) {
       const int g0 = c0 >> 3;
@@ -481,7 +454,6 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
       for (int t = 0; t < 4; ++t)
         st_slope(e.slope(l, g0 + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
                  e.pol);
-      if constexpr (!kF16) store_res(e, l, c0, rw);
     }
   }
 }
@@ -531,7 +503,7 @@ __device__ __forceinline__ void layer0(const Epi &e) {
 #pragma unroll 1
   for (int cc = 0; cc < 8; ++cc) {
     const int c0 = 256 * e.ch + 32 * cc;
-    uint32_t hw[16], sw[16], rw[8];
+    uint32_t hw[16], sw[16];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const float4 bq = lds4(kOffBias, c0 + 4 * q);
@@ -548,12 +520,17 @@ __device__ __forceinline__ void layer0(const Epi &e) {
         act(z, e.neg_bl2e, e.inv_beta, hv[u], sv[u]);
         if (FEEDS_SKIP) hv[u] = (c < kNShort) ? hv[u] * kInvSqrt2 : 0.0f;
       }
-      hw[2 * q] = Op<kF16>::pack(hv[0], hv[1]);
-      hw[2 * q + 1] = Op<kF16>::pack(hv[2], hv[3]);
-      if constexpr (!kF16)
-        rw[q] = res_pair(hv[0], hv[1], hw[2 * q]) | (res_pair(hv[2], hv[3], hw[2 * q + 1]) << 16);
-      sw[2 * q] = Op<true>::pack(sv[0], sv[1]);
-      sw[2 * q + 1] = Op<true>::pack(sv[2], sv[3]);
+      if constexpr (kF16) {
+        hw[2 * q] = Op<kF16>::pack(hv[0], hv[1]);
+        hw[2 * q + 1] = Op<kF16>::pack(hv[2], hv[3]);
+        sw[2 * q] = Op<true>::pack(sv[0], sv[1]);
+        sw[2 * q + 1] = Op<true>::pack(sv[2], sv[3]);
+      } else {
+        sw[2 * q] = h2_bits(__floats2half2_rn(hv[0], hv[1]));
+        sw[2 * q + 1] = h2_bits(__floats2half2_rn(hv[2], hv[3]));
+        hw[2 * q] = bf16_of_h2(rnd8_h2(sw[2 * q]));
+        hw[2 * q + 1] = bf16_of_h2(rnd8_h2(sw[2 * q + 1]));
+      }
     }
     store_a_chunk(e.A, e.r, c0, hw);
     if constexpr (kSave) save_chunk(e, e.save_h, 0, c0, hw);
@@ -561,35 +538,45 @@ __device__ __forceinline__ void layer0(const Epi &e) {
     for (int t = 0; t < 4; ++t)
       st_slope(e.slope(0, (c0 >> 3) + t), make_uint4(sw[4 * t], sw[4 * t + 1], sw[4 * t + 2], sw[4 * t + 3]),
                e.pol);
-    if constexpr (!kF16) store_res(e, 0, c0, rw);
   }
 }
 
 // One 32-column chunk of a reverse epilogue: delta_{l-1} = slope_{l-1} * g.
 // The 16 packed words of the next A operand go to `dw` (unused for TO_INPUT).
-// In the BF16 form it also adds this chunk's share of the first-order
-// correction of f for the rounding of A operand l-1: raw = W_l^T delta_l is
-// df/dA_{l-1} (before the skip connection's 1/sqrt(2) split), `rs` holds the
-// chunk's 32 scaled residuals.  The products are summed in packed FP16 (the
-// residuals are exact there; df/dA saturates at 65504 and a non-finite chunk
-// sum is dropped).
+// In the BF16 form the slab holds the FP16 activation a of layer l-1 (its
+// A operand before rounding): the slope is sigmoid(beta z) = 1 - e^{-beta h}
+// (h = a, or sqrt(2) a for the layer feeding the skip connection), and the
+// chunk also adds its share of the first-order correction of f for the
+// rounding of A_{l-1}: raw = W_l^T delta_l is df/dA_{l-1} (before the skip
+// connection's 1/sqrt(2) split) and a - rnd8(a) the residual of the rounded
+// operand.  The products are summed in packed FP16 with the residuals scaled
+// by 2^10 (exact; df/dA saturates at 65504 and a non-finite chunk sum is
+// dropped).
 template <bool kF16, bool AT_SKIP, bool MAKES_SKIP_DELTA, bool TO_INPUT>
 __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (&raw)[32],
-                                          const uint4 (&sl)[4], const uint4 (&rs)[2], Acc &acc,
-                                          uint32_t (&dw)[16]) {
+                                          const uint4 (&sl)[4], Acc &acc, uint32_t (&dw)[16]) {
+  float sv_all[32];
   if constexpr (!kF16) {
     __half2 c0h = __float2half2_rn(0.0f), c1h = c0h;
+    const __half2 kexp = AT_SKIP ? e.kh.neg_bl2e_s2 : e.kh.neg_bl2e;
+    const __half2 one = __float2half2_rn(1.0f);
+    const __half2 k1024 = __float2half2_rn(1024.0f);     // keeps the products above FP16's subnormals
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const uint32_t w = comp_u(rs[q >> 2], q & 3);     // residual bytes of columns 4q..4q+3
-      c0h = __hfma2(e4m3x2_to_h2(w & 0xffffu),
-                    h2_sat(__uint_as_float(raw[4 * q]), __uint_as_float(raw[4 * q + 1])), c0h);
-      c1h = __hfma2(e4m3x2_to_h2(w >> 16),
-                    h2_sat(__uint_as_float(raw[4 * q + 2]), __uint_as_float(raw[4 * q + 3])), c1h);
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t hb = comp_u(sl[j >> 2], j & 3);      // activations of columns 2j, 2j+1
+      const __half2 a = *reinterpret_cast<const __half2 *>(&hb);
+      const uint32_t ab = rnd8_h2(hb);
+      const __half2 r = __hmul2(__hsub2(a, *reinterpret_cast<const __half2 *>(&ab)), k1024);
+      const __half2 g = h2_sat(__uint_as_float(raw[2 * j]), __uint_as_float(raw[2 * j + 1]));
+      if (j & 1) c1h = __hfma2(r, g, c1h);
+      else c0h = __hfma2(r, g, c0h);
+      const float2 s2 = __half22float2(__hsub2(one, h2_ex2(__hmul2(a, kexp))));
+      sv_all[2 * j] = s2.x;
+      sv_all[2 * j + 1] = s2.y;
     }
     const float2 cs = __half22float2(__hadd2(c0h, c1h));
     const float c = cs.x + cs.y;
-    if (isfinite(c)) acc.f = fmaf(c, 1.0f / kResScale, acc.f);
+    if (isfinite(c)) acc.f = fmaf(c, 1.0f / 1024.0f, acc.f);
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -604,10 +591,16 @@ __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (
       w_b = lds4(kOffW0, 3 * (c0 + 4 * q) + 4);
       w_c = lds4(kOffW0, 3 * (c0 + 4 * q) + 8);
     }
-    const uint32_t swords[2] = {comp_u(sl[q >> 1], 2 * (q & 1)), comp_u(sl[q >> 1], 2 * (q & 1) + 1)};
-    const float2 sa = Op<true>::unpack(swords[0]);     // slopes are FP16 in the slab
-    const float2 sb = Op<true>::unpack(swords[1]);
-    const float sv[4] = {sa.x, sa.y, sb.x, sb.y};
+    float sv[4];
+    if constexpr (kF16) {
+      const uint32_t swords[2] = {comp_u(sl[q >> 1], 2 * (q & 1)), comp_u(sl[q >> 1], 2 * (q & 1) + 1)};
+      const float2 sa = Op<true>::unpack(swords[0]);     // slopes are FP16 in the slab
+      const float2 sb = Op<true>::unpack(swords[1]);
+      sv[0] = sa.x; sv[1] = sa.y; sv[2] = sb.x; sv[3] = sb.y;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sv[u] = sv_all[4 * q + u];
+    }
     float dv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -634,22 +627,15 @@ __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (
   }
 }
 
-// After a chunk's slopes have been consumed, drop their L2 lines: the warp's
-// 32 rows x 4 slope groups (columns c0..c0+31) cover 16 lines of 128 bytes,
-// one per lane 0..15; in the BF16 form its 32 rows x 2 residual groups cover
-// 8 more, one per lane 16..23.
-template <bool kF16>
+// After a chunk's slab words have been consumed, drop their L2 lines: the
+// warp's 32 rows x 4 groups (columns c0..c0+31) cover 16 lines of 128 bytes,
+// one per lane 0..15.
 __device__ __forceinline__ void discard_chunk(const Epi &e, int l, int c0) {
   __syncwarp();
   if (e.lane < 16) {
     const int g = (c0 >> 3) + (e.lane >> 2);
     const int row0 = (e.r & ~31) + 8 * (e.lane & 3);
     const uint8_t *line = e.slab + (((size_t)l * (kW / 8) + g) * kM + row0) * 16;
-    l2_discard_line(line);
-  } else if (!kF16 && e.lane < 24) {
-    const int g = (c0 >> 4) + ((e.lane - 16) >> 2);
-    const int row0 = (e.r & ~31) + 8 * (e.lane & 3);
-    const uint8_t *line = e.resb + (((size_t)l * (kW / 16) + g) * kM + row0) * 16;
     l2_discard_line(line);
   }
 }
@@ -663,46 +649,35 @@ __device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, G
                                          uint32_t mid) {
   uint32_t ra[32], rb[32];
   uint4 sa[4], sb[4];
-  uint4 xa[2], xb[2];        // BF16 form: residuals of the chunk (unused in FP16)
   const int cbase = 256 * h + 128 * e.ch;
   const int g0 = cbase >> 3;
-  auto load_res = [&](uint4 (&x)[2], int c0) {
-    if constexpr (!kF16) {
-      x[0] = *e.res(l - 1, c0 >> 4);
-      x[1] = *e.res(l - 1, (c0 >> 4) + 1);
-    }
-  };
 #pragma unroll
   for (int t = 0; t < 4; ++t) sa[t] = *e.slope(l - 1, g0 + t);
-  load_res(xa, cbase);
   tmem_ld32_async(e.t_row + cbase, ra);
 #pragma unroll 1
   for (int cc = 0; cc < 4; cc += 2) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) sb[t] = *e.slope(l - 1, g0 + 4 * (cc + 1) + t);
-    load_res(xb, cbase + 32 * (cc + 1));
     uint32_t dw[16];
     tmem_wait_ld(ra);
     tmem_ld32_async(e.t_row + cbase + 32 * (cc + 1), rb);
-    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * cc, ra, sa, xa, acc, dw);
+    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * cc, ra, sa, acc, dw);
     if (!TO_INPUT) {
       gate.pass(cc >> 1);
       store_a_chunk(e.A, e.r, cbase + 32 * cc, dw);
     }
     if constexpr (kSave) save_chunk(e, e.save_d, l - 1, cbase + 32 * cc, dw);   // delta_{l-1}
-    discard_chunk<kF16>(e, l - 1, cbase + 32 * cc);
+    discard_chunk(e, l - 1, cbase + 32 * cc);
     if (cc + 2 < 4) {
 #pragma unroll
       for (int t = 0; t < 4; ++t) sa[t] = *e.slope(l - 1, g0 + 4 * (cc + 2) + t);
-      load_res(xa, cbase + 32 * (cc + 2));
     }
     tmem_wait_ld(rb);
     if (cc + 2 < 4) tmem_ld32_async(e.t_row + cbase + 32 * (cc + 2), ra);
-    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * (cc + 1), rb, sb, xb, acc,
-                                                         dw);
+    bwd_chunk<kF16, AT_SKIP, MAKES_SKIP_DELTA, TO_INPUT>(e, cbase + 32 * (cc + 1), rb, sb, acc, dw);
     if (!TO_INPUT) store_a_chunk(e.A, e.r, cbase + 32 * (cc + 1), dw);
     if constexpr (kSave) save_chunk(e, e.save_d, l - 1, cbase + 32 * (cc + 1), dw);
-    discard_chunk<kF16>(e, l - 1, cbase + 32 * (cc + 1));
+    discard_chunk(e, l - 1, cbase + 32 * (cc + 1));
     if (cc == 0 && mid != 0u) epi_arrive(mid, e.lane);
   }
 }
@@ -928,8 +903,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     Epi e;
     e.A = A;
     e.slab = reinterpret_cast<uint8_t *>(prm.scratch) +
-             (size_t)blockIdx.x * (size_t)(L - 1) * kW * kM * kSlabElemBytes<kF16>;
-    e.resb = e.slab + (size_t)(L - 1) * kW * kM * 2;
+             (size_t)blockIdx.x * (size_t)(L - 1) * kW * kM * 2;
     e.t_row = tmem + ((uint32_t)(32 * q) << 16);
     e.r = r;
     e.ch = ch;
@@ -943,6 +917,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     e.kh.neg_bl2e = __float2half2_rn(-prm.beta * 1.4426950408889634f);
     e.kh.inv_beta = __float2half2_rn(1.0f / prm.beta);
     e.kh.half_beta = __float2half2_rn(0.5f * prm.beta);
+    e.kh.neg_bl2e_s2 = __float2half2_rn(-prm.beta * 1.4426950408889634f * kSqrt2);
     e.lane = lane;
     const bool prefetcher = (warp == kEpiWarp0 && lane == 0);
     uint32_t d_phase = 0, x_phase = 0;
@@ -1006,10 +981,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- Jacobian-transpose chain: layers L-1 .. 1 ----
       for (int l = L - 1; ok && l >= 1; --l) {
         // bring this layer's slopes (128 KB of this CTA) into L2 while its products run
-        if (prefetcher) {
-          l2_prefetch_bulk(e.slab + (size_t)(l - 1) * kW * kM * 2, kW * kM * 2);
-          if (!kF16) l2_prefetch_bulk(e.resb + (size_t)(l - 1) * kW * kM, kW * kM);
-        }
+        if (prefetcher) l2_prefetch_bulk(e.slab + (size_t)(l - 1) * kW * kM * 2, kW * kM * 2);
         const bool at = (l == skip), makes = (l - 1 == skip), to_input = (l == 1);
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
@@ -1156,9 +1128,9 @@ int query_tc16_grid(int width, int64_t n, int num_sms) {
 
 size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid, bool fp16) {
   (void)width;
-  // 16-bit slopes, plus the e4m3 rounding residuals in the BF16 form
-  return (size_t)grid * (size_t)(n_hidden - 1) * kW * kM *
-         (size_t)(fp16 ? kSlabElemBytes<true> : kSlabElemBytes<false>);
+  (void)fp16;
+  // one 16-bit word per element: the slope (FP16 form) or the activation (BF16 form)
+  return (size_t)grid * (size_t)(n_hidden - 1) * kW * kM * 2;
 }
 
 template <bool kF16, bool kSave>
