@@ -73,7 +73,7 @@ def build(verbose=False, extra=()):
             sys.stderr.write(log)
     tmp = LIB + ".tmp"
     cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
-    cmd = [nvcc, "-shared", "-o", tmp, *objs, *ARCH, "--cudart", "shared", "-lcublas",
+    cmd = [nvcc, "-shared", "-o", tmp, *objs, *ARCH, "--cudart", "shared",
            "-Xlinker", f"-rpath,{cudalib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

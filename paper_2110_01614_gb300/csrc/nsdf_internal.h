@@ -113,6 +113,27 @@ int fp32_ctas_per_sm(int width, int pt, bool ff = false);
 size_t fp32_scratch_bytes_pt(int width, int pt, int n_hidden, int grid);
 cudaError_t launch_query_fp32_grouped(const QueryParams &p, int pt, int grid, cudaStream_t s);
 
+// Weight-gradient products of the fitting loss on the tensor cores
+// (wgrad_tc.cu): for product i, G[gslot[i]] (W x W, row-major [n][k], FP32)
+// = sum over the n_pad points of D(point)[n] H(point)[k], with D rows
+// save_d[dslot[i]] and H rows save_h[hslot[i]] (16-bit, [slot][n_pad][W]).
+// ws holds layers x S x W x W floats of split partials.
+struct WgradJob {
+  const uint16_t *save_h, *save_d;
+  int64_t h_rows, d_rows;   // rows of the two saved arrays (slots x n_pad)
+  int64_t n_pad;
+  int W, layers, S;
+  int hslot[64], dslot[64], gslot[64];
+  float *ws, *G;
+  int *err;
+  long long wait_budget;
+  bool fp16;
+  int num_sms;
+};
+int wgrad_splits(int W, int layers, int64_t n_pad, int num_sms);
+bool wgrad_supported(int W);
+cudaError_t launch_wgrad_tc(const WgradJob &job, cudaStream_t s);
+
 bool query_tc16_supported(int width, int n_hidden, int skip);
 bool make_tc16_tmaps(NetDevice &net, int width, int n_hidden, bool fp16);
 cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bool fp16,

@@ -10,8 +10,9 @@
 // every layer's A operand out (h_l on the forward pass, delta_l on the
 // reverse pass, 16-bit, one row per point); the rows of delta are then
 // multiplied by a_i (a sign flip or a zero: exact in 16 bits), the
-// hidden-layer weight gradients are plain GEMMs over the points (cuBLAS, FP32
-// accumulation), and the remaining sums (biases, W_0 on p, the skip layer's
+// hidden-layer weight gradients are contractions over the points on the
+// tensor cores (wgrad_tc.cu: tcgen05, FP32 accumulation in TMEM, split over
+// the points and reduced in a fixed order), and the remaining sums (biases, W_0 on p, the skip layer's
 // columns on p / sqrt(2), w_out and b_out) are FP32 per-block partial sums
 // reduced in block order, so the result does not depend on scheduling.
 //
@@ -20,8 +21,6 @@
 // features, saved in the kernel's permuted column order) gets its own GEMM,
 // whose columns are put back in feature order; the frequencies B are not
 // trained (random Fourier features) and get a zero gradient.
-
-#include <cublas_v2.h>
 
 #include <cmath>
 #include <new>
@@ -234,8 +233,8 @@ struct TrainState {
   float4 *ns = nullptr;
   float *a = nullptr, *loss_part = nullptr, *part = nullptr, *small = nullptr, *G = nullptr,
         *loss_tmp = nullptr;
+  float *ws = nullptr;   // split partials of the weight-gradient products
   int64_t part_floats = 0;
-  cublasHandle_t blas = nullptr;
 };
 
 void free_all(TrainState *t) {
@@ -248,9 +247,10 @@ void free_all(TrainState *t) {
   cudaFree(t->small);
   cudaFree(t->G);
   cudaFree(t->loss_tmp);
+  cudaFree(t->ws);
   t->save_h = t->save_d = nullptr;
   t->ns = nullptr;
-  t->a = t->loss_part = t->part = t->small = t->G = t->loss_tmp = nullptr;
+  t->a = t->loss_part = t->part = t->small = t->G = t->loss_tmp = t->ws = nullptr;
   t->cap = 0;
 }
 
@@ -271,7 +271,6 @@ void train_state_free(void *p) {
   if (!p) return;
   TrainState *t = static_cast<TrainState *>(p);
   free_all(t);
-  if (t->blas) cublasDestroy(t->blas);
   delete t;
 }
 
@@ -288,7 +287,7 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
   const NetDevice *net = nullptr;
   nsdf_status st = ctx_query_setup(ctx, &p, &num_sms, &W, &L, &tc16, &fp16, &net);
   if (st != NSDF_OK) return st;
-  if (!tc16) return NSDF_ERR_UNSUPPORTED;   // FP32 contexts: nsdf_backward
+  if (!tc16 || !wgrad_supported(W)) return NSDF_ERR_UNSUPPORTED;   // FP32 contexts: nsdf_backward
   const bool ff = p.ff > 0;                  // the Fourier-feature ReLU kernel
   if (n == 0) return NSDF_ERR_INVALID_ARG;
   if (!pts || !targets) return NSDF_ERR_INVALID_ARG;
@@ -310,20 +309,18 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
     // ff: h_0 .. h_{L-1} and the features (slot L); G for every layer
     const size_t hslots = ff ? (size_t)L + 1 : (size_t)L;
     const size_t gslots = ff ? (size_t)L : (size_t)(L > 1 ? L - 1 : 1);
+    const int S = wgrad_splits(W, (int)gslots, n_pad, num_sms);
     bool ok = dalloc(&t->save_h, hslots * rows * W) && dalloc(&t->save_d, (size_t)L * rows * W) &&
               dalloc(&t->ns, rows) && dalloc(&t->a, rows) &&
               dalloc(&t->loss_part, (rows + 255) / 256) &&
               dalloc(&t->part, (size_t)jobs * nb * W * 3) && dalloc(&t->small, (size_t)jobs * W * 3) &&
-              dalloc(&t->G, gslots * W * W) && dalloc(&t->loss_tmp, 1);
+              dalloc(&t->G, gslots * W * W) && dalloc(&t->loss_tmp, 1) &&
+              dalloc(&t->ws, gslots * (size_t)S * W * W);
     if (!ok) {
       free_all(t);
       return NSDF_ERR_OOM;
     }
     t->cap = n_pad;
-  }
-  if (!t->blas && cublasCreate(&t->blas) != CUBLAS_STATUS_SUCCESS) {
-    t->blas = nullptr;
-    return NSDF_ERR_CUDA;
   }
   // 1. the training form of the query: f per point, every A operand saved
   p.pts = reinterpret_cast<const float4 *>(pts);
@@ -344,22 +341,30 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
   const int64_t vecs = (int64_t)L * n_pad * W / 8;
   scale_rows_kernel<<<8 * num_sms, 256, 0, s>>>(reinterpret_cast<uint4 *>(t->save_d), vecs, n_pad,
                                                 W, t->a);
-  // 3. hidden-layer weight gradients: G_l[n][k] = sum_i delta_l(i)[n] h_{l-1}(i)[k]
-  if (cublasSetStream(t->blas, s) != CUBLAS_STATUS_SUCCESS) return NSDF_ERR_CUDA;
-  const cudaDataType_t dt = fp16 ? CUDA_R_16F : CUDA_R_16BF;
-  const float one = 1.f, zero = 0.f;
-  for (int l = ff ? 0 : 1; l < L; ++l) {
+  // 3. hidden-layer weight gradients on the tensor cores:
+  //    G_l[n][k] = sum_i delta_l(i)[n] h_{l-1}(i)[k]
+  WgradJob job{};
+  job.save_h = t->save_h;
+  job.save_d = t->save_d;
+  job.h_rows = (int64_t)(ff ? L + 1 : L) * n_pad;
+  job.d_rows = (int64_t)L * n_pad;
+  job.n_pad = n_pad;
+  job.W = W;
+  job.layers = 0;
+  for (int l = ff ? 0 : 1; l < L; ++l, ++job.layers) {
     // layer l reads h_{l-1} (for ff layer 0: the features, slot L)
-    const int hs = (ff && l == 0) ? L : l - 1;
-    const uint16_t *H = t->save_h + (size_t)hs * n_pad * W;
-    const uint16_t *D = t->save_d + (size_t)l * n_pad * W;
-    float *Gl = t->G + (size_t)(ff ? l : l - 1) * W * W;
-    // column-major: C (W x W) = H^T-view (W x n_pad) * D-view^T (n_pad x W)
-    if (cublasGemmEx(t->blas, CUBLAS_OP_N, CUBLAS_OP_T, W, W, (int)n_pad, &one, H, dt, W, D, dt, W,
-                     &zero, Gl, CUDA_R_32F, W, CUBLAS_COMPUTE_32F,
-                     CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
-      return NSDF_ERR_CUDA;
+    job.hslot[job.layers] = (ff && l == 0) ? L : l - 1;
+    job.dslot[job.layers] = l;
+    job.gslot[job.layers] = ff ? l : l - 1;
   }
+  job.S = wgrad_splits(W, job.layers, n_pad, num_sms);
+  job.ws = t->ws;
+  job.G = t->G;
+  job.err = p.err;
+  job.wait_budget = p.wait_budget;
+  job.fp16 = fp16;
+  job.num_sms = num_sms;
+  if (job.layers > 0 && launch_wgrad_tc(job, s) != cudaSuccess) return NSDF_ERR_CUDA;
   // 4. the small sums, reduced in block order
   small_partials_kernel<<<dim3(nb, jobs), W / 8, 0, s>>>(t->save_h, t->save_d, p.pts, t->a, L, W,
                                                          p.skip, p.ff, n, n_pad, fp16 ? 1 : 0,
