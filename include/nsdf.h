@@ -106,8 +106,12 @@ size_t nsdf_num_params(const nsdf_arch *arch);
  * this build handles (arch, prec): FP32 takes widths 32, 64, 128, 256 and
  * 512 with either activation and Fourier features; BF16 and FP16 take
  * softplus networks of width 512 with at least two hidden layers and no
- * Fourier features, and the Fourier-feature ReLU networks of Sec. 4.3 of
- * width 256 (ff_freqs = 128) with 1 to 8 layers and no skip layer.  In the
+ * Fourier features, softplus networks of width 64 with 2 to 7 hidden layers
+ * and no skip layer or Fourier features (their forward products take split
+ * BF16 operands, hi + lo, in the BF16 form: one BF16 rounding of 64-wide
+ * weights alone moves f by up to ~3e-3), and the Fourier-feature ReLU
+ * networks of Sec. 4.3 of width 256 (ff_freqs = 128) with 1 to 8 layers and
+ * no skip layer.  In the
  * 16-bit forms a ReLU slope is decided on the 16-bit network's own
  * pre-activations: near z = 0 it can differ from an FP32 or exact
  * evaluation, and with it the normal.
@@ -201,7 +205,8 @@ nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n,
  * dL/dtheta; loss (device float, nullable) receives L.  The derivative of
  * |f - d| is taken as sign(f - d), 0 at equality.  The hidden-layer weight
  * gradients are products over the points of the kernel's 16-bit deltas and
- * activations with FP32 accumulation (cuBLAS); the other sums are FP32 and
+ * activations on the tensor cores with FP32 accumulation (the library's own
+ * tcgen05 kernel, widths 256 and 512); the other sums are FP32 and
  * reduced in a fixed order, so repeated calls give identical results.  Uses
  * about 2 n_hidden x width x 2 bytes of device memory per point, allocated on
  * the first call and when n grows.  Fourier-feature ReLU contexts (Sec. 4.3)
@@ -223,9 +228,10 @@ nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n,
  * max_total bounds offsets[k] + counts[k] (a violating entry is skipped and
  * reported by nsdf_sync_status as NSDF_ERR_INVALID_ARG) and sizes the launch.
  * out_n_sdf nullable; points outside every range are left untouched.
- * Arithmetic: FP32 (the FP32 fused kernel) for every context except the
- * 16-bit Fourier-feature ReLU ones, which run the tensor-core kernel of
- * their precision with the same results per point as nsdf_collide.  The
+ * Arithmetic: FP32 contexts run the FP32 fused kernel; 16-bit width-64
+ * softplus and Fourier-feature ReLU contexts run the tensor-core kernel of
+ * their shape and precision with the same results per point as
+ * nsdf_collide.  The
  * first call with a given max_total may allocate scratch: make it before
  * capturing the call into a graph.
  */
@@ -260,7 +266,9 @@ nsdf_status nsdf_query_grouped_T(nsdf_ctx *ctx, const float *pts,
  * thread) and chosen[1] (CTAs per SM) when chosen is not NULL.  16-bit
  * Fourier-feature contexts have one grouped shape (a 128-point tile per
  * CTA, one CTA per SM, on tensor cores): the problem runs once and chosen
- * receives {0, 1}.  Runs the
+ * receives {0, 1}.  16-bit width-64 contexts (two 128-point tiles per CTA
+ * on tensor cores) time every CTAs-per-SM count that fits and report
+ * {0, CTAs per SM}.  Runs the
  * problem several times (outputs are overwritten with correct results) and
  * synchronises `stream`; do not call it during stream capture.
  */
@@ -271,7 +279,8 @@ nsdf_status nsdf_autotune_grouped(nsdf_ctx *ctx, const float *pts,
                                   int *chosen);
 
 /* Set the grouped launch configuration directly (e.g. from a saved tuning):
- * points_per_thread 4 or 8, ctas_per_sm >= 0 (0: as many as fit). */
+ * points_per_thread 4 or 8 (FP32 contexts; 16-bit contexts, whose kernels
+ * have one tile shape, also accept 0), ctas_per_sm >= 0 (0: as many as fit). */
 nsdf_status nsdf_set_grouped_config(nsdf_ctx *ctx, int points_per_thread,
                                     int ctas_per_sm);
 

@@ -93,6 +93,7 @@ struct PackTargets {
   float *ffB, *ff0_t, *ff0;
   uint16_t *fwd16, *bwd16;
   int fp16;   // 16-bit copies as FP16 (1) or BF16 (0)
+  uint16_t *fwd16_lo;   // nullable: BF16 residual W - bf16(W) of the hidden layers
 };
 
 __device__ __forceinline__ uint16_t to16(float v, int fp16) {
@@ -154,6 +155,10 @@ __global__ void pack_weights_kernel(const float *__restrict__ blob, PackPlan pla
       const int64_t o16 = plan.ff > 0 ? o + per : o;
       net.fwd16[o16] = to16(w_rc, net.fp16);   // [n=r][k=c]
       net.bwd16[o16] = to16(w_cr, net.fp16);   // [k=r][n=c]
+      if (net.fwd16_lo) {
+        const uint16_t hi = to16(w_rc, 0);
+        net.fwd16_lo[o16] = to16(w_rc - __uint_as_float((uint32_t)hi << 16), 0);
+      }
     }
   }
 }
@@ -221,13 +226,20 @@ bool use_bf16(const nsdf_ctx *ctx) { return ctx->prec == NSDF_BF16 || ctx->prec 
 // 16-bit Fourier-feature ReLU contexts run query_tc16_ff.cu.
 bool use_tc16_ff(const nsdf_ctx *ctx) { return use_bf16(ctx) && ctx->arch.ff_freqs > 0; }
 
+// 16-bit width-64 softplus contexts run query_tc16_w64.cu (no scratch).
+bool use_w64(const nsdf_ctx *ctx) {
+  return use_bf16(ctx) && ctx->arch.ff_freqs == 0 && ctx->arch.width == 64;
+}
+
 int query_grid(const nsdf_ctx *ctx, int64_t n) {
+  if (use_w64(ctx)) return ctx->num_sms;
   if (use_tc16_ff(ctx)) return query_tc16_ff_grid(n, ctx->num_sms);
   if (use_bf16(ctx)) return query_tc16_grid(ctx->arch.width, n, ctx->num_sms);
   return query_fp32_grid(ctx->arch.width, n, ctx->num_sms, ctx->arch.ff_freqs > 0);
 }
 
 size_t query_scratch(const nsdf_ctx *ctx, int grid) {
+  if (use_w64(ctx)) return 0;
   if (use_tc16_ff(ctx)) return query_tc16_ff_scratch_bytes(grid);
   if (use_bf16(ctx))
     return query_tc16_scratch_bytes(ctx->arch.width, ctx->arch.n_hidden, grid, ctx->prec == NSDF_FP16);
@@ -252,7 +264,7 @@ nsdf_status ensure_scratch(nsdf_ctx *ctx, size_t bytes) {
 void fill_net(const nsdf_ctx *ctx, int net, QueryParams &p) {
   const NetDevice &d = ctx->nets[net];
   p.w0 = d.w0; p.bias = d.bias; p.fwd_t = d.fwd_t; p.bwd = d.bwd; p.wout = d.wout; p.bout = d.bout;
-  p.fwd16 = d.fwd16; p.bwd16 = d.bwd16;
+  p.fwd16 = d.fwd16; p.bwd16 = d.bwd16; p.fwd16_lo = d.fwd16_lo;
   p.ffB = d.ffB; p.ff0_t = d.ff0_t; p.ff0 = d.ff0;
   p.width = ctx->arch.width;
   p.n_hidden = ctx->arch.n_hidden;
@@ -266,6 +278,7 @@ void fill_net(const nsdf_ctx *ctx, int net, QueryParams &p) {
 }
 
 cudaError_t launch_query(const nsdf_ctx *ctx, int net, const QueryParams &p, cudaStream_t s) {
+  if (use_w64(ctx)) return launch_query_w64(p, ctx->prec == NSDF_FP16, ctx->num_sms, 0, s);
   if (use_tc16_ff(ctx))
     return launch_query_tc16_ff(p, ctx->nets[net], ctx->prec == NSDF_FP16, ctx->num_sms, s);
   if (use_bf16(ctx))
@@ -293,7 +306,7 @@ nsdf_status ensure_pipeline(nsdf_ctx *ctx) {
   // per CTA and iteration) get a whole number of grid-wide iterations, so no
   // chunk ends in a partly filled wave of tiles
   int64_t chunk = 1 << 18;
-  if (use_bf16(ctx)) {
+  if (use_bf16(ctx) && !use_w64(ctx)) {
     const int64_t wave = (int64_t)query_grid(ctx, chunk) * 128;
     const int64_t waves = (chunk + wave / 2) / wave;
     chunk = (waves > 0 ? waves : 1) * wave;
@@ -458,7 +471,8 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
                          query_tc16_ff_supported(arch->width, arch->n_hidden, arch->ff_freqs,
                                                  arch->activation == NSDF_ACT_RELU);
     const bool softplus = arch->ff_freqs == 0 && arch->activation == NSDF_ACT_SOFTPLUS &&
-                          query_tc16_supported(arch->width, arch->n_hidden, arch->skip_layer);
+                          (query_tc16_supported(arch->width, arch->n_hidden, arch->skip_layer) ||
+                           query_w64_supported(arch->width, arch->n_hidden, arch->skip_layer));
     if (!ff_relu && !softplus) return NSDF_ERR_UNSUPPORTED;
   }
   nsdf_ctx *ctx = new (std::nothrow) nsdf_ctx;
@@ -505,6 +519,7 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
       } else {
         st = ctx_alloc(ctx, &d.fwd16, hid);
         if (st == NSDF_OK) st = ctx_alloc(ctx, &d.bwd16, hid);
+        if (st == NSDF_OK && prec == NSDF_BF16 && W == 64) st = ctx_alloc(ctx, &d.fwd16_lo, hid);
       }
     }
   }
@@ -516,7 +531,8 @@ nsdf_status nsdf_create(const nsdf_arch *arch, nsdf_precision prec, int n_nets, 
     std::vector<NetPtrs> h(n_nets);
     for (int k = 0; k < n_nets; ++k) {
       const NetDevice &d = ctx->nets[k];
-      h[k] = NetPtrs{d.w0, d.bias, d.fwd_t, d.bwd, d.wout, d.bout, d.ffB, d.ff0_t, d.ff0};
+      h[k] = NetPtrs{d.w0, d.bias, d.fwd_t, d.bwd, d.wout, d.bout, d.ffB, d.ff0_t, d.ff0,
+                     d.fwd16, d.fwd16_lo};
     }
     st = map_err(cudaMemcpy(ctx->d_netptrs, h.data(), sizeof(NetPtrs) * n_nets,
                             cudaMemcpyHostToDevice));
@@ -583,7 +599,8 @@ nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w, size_t n_f
   }
   const NetDevice &d = ctx->nets[net];
   PackTargets tg{d.w0,    d.bias,  d.fwd_t, d.bwd,   d.wout,  d.bout, d.ffB,
-                 d.ff0_t, d.ff0,   d.fwd16, d.bwd16, ctx->prec == NSDF_FP16 ? 1 : 0};
+                 d.ff0_t, d.ff0,   d.fwd16, d.bwd16, ctx->prec == NSDF_FP16 ? 1 : 0,
+                 d.fwd16_lo};
   pack_weights_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(src, plan, tg);
   cudaError_t e = last_err();
   if (tmp) {
@@ -594,7 +611,8 @@ nsdf_status nsdf_load_weights(nsdf_ctx *ctx, int net, const float *w, size_t n_f
   if (e != cudaSuccess) return map_err(e);
   const bool fp16 = ctx->prec == NSDF_FP16;
   if (use_tc16_ff(ctx) ? !make_tc16_ff_tmaps(ctx->nets[net], a.n_hidden, net == 0 ? ctx->n_nets : 1, fp16)
-                       : use_bf16(ctx) && !make_tc16_tmaps(ctx->nets[net], a.width, a.n_hidden, fp16))
+                       : use_bf16(ctx) && !use_w64(ctx) &&
+                             !make_tc16_tmaps(ctx->nets[net], a.width, a.n_hidden, fp16))
     return NSDF_ERR_CUDA;
   ctx->nets[net].loaded = true;
   return NSDF_OK;
@@ -790,8 +808,37 @@ nsdf_status grouped_launch_tc16_ff(nsdf_ctx *ctx, const GroupedArgs &g, cudaStre
   return map_err(launch_query_tc16_ff(p, ctx->nets[0], ctx->prec == NSDF_FP16, ctx->num_sms, s));
 }
 
+// Grouped launch of the 16-bit width-64 kernel: 128-point tiles, each
+// network's tile count rounded up to even (the two warpgroups of a CTA take
+// a pair of tiles of one network); cps = CTAs per SM (0: as many as fit).
+nsdf_status grouped_launch_w64(nsdf_ctx *ctx, const GroupedArgs &g, int cps, cudaStream_t s) {
+  cudaError_t e = launch_build_tile_list(g.offsets, g.counts, ctx->n_nets, 128, g.max_total,
+                                         ctx->d_tile_start, ctx->d_err, s, 2);
+  if (e != cudaSuccess) return map_err(e);
+  if (g.T) {
+    e = launch_body_transforms(g.T, ctx->n_nets, ctx->d_body, ctx->d_err, s);
+    if (e != cudaSuccess) return map_err(e);
+  }
+  QueryParams p{};
+  fill_net(ctx, 0, p);
+  p.pts = reinterpret_cast<const float4 *>(g.pts);
+  p.n = g.max_total;
+  p.collide = 1;
+  p.eps = g.eps;
+  p.out_pts = reinterpret_cast<float4 *>(g.out_pts);
+  p.out_n_sdf = reinterpret_cast<float4 *>(g.out_n_sdf);
+  p.g_nets = ctx->n_nets;
+  p.g_offsets = g.offsets;
+  p.g_counts = g.counts;
+  p.g_tile_start = ctx->d_tile_start;
+  p.g_netptrs = ctx->d_netptrs;
+  p.g_T = g.T ? ctx->d_body : nullptr;
+  return map_err(launch_query_w64(p, ctx->prec == NSDF_FP16, ctx->num_sms, cps, s));
+}
+
 nsdf_status grouped_launch(nsdf_ctx *ctx, const GroupedArgs &g, int pt, int cps, cudaStream_t s) {
   if (use_tc16_ff(ctx)) return grouped_launch_tc16_ff(ctx, g, s);
+  if (use_w64(ctx)) return grouped_launch_w64(ctx, g, cps, s);
   const nsdf_arch &a = ctx->arch;
   const int grid = grouped_grid(ctx, pt, cps, g.max_total);
   nsdf_status st = ensure_scratch(ctx, fp32_scratch_bytes_pt(a.width, pt, a.n_hidden, grid));
@@ -870,9 +917,14 @@ nsdf_status nsdf_autotune_grouped(nsdf_ctx *ctx, const float *pts, const int64_t
     return NSDF_ERR_CUDA;
   float best = 3.0e38f;
   int best_pt = ctx->grouped_pt, best_cps = ctx->grouped_cps;
+  // FP32 kernel: points per thread (4 or 8) and CTAs per SM; 16-bit width-64
+  // kernel: CTAs per SM (its tiles are 128 points, two per CTA)
+  const bool w64 = use_w64(ctx);
   const int pts_opts[2] = {4, 8};
-  for (int pt : pts_opts) {
-    const int fit = fp32_ctas_per_sm(ctx->arch.width, pt, ctx->arch.ff_freqs > 0);
+  for (int oi = 0; oi < (w64 ? 1 : 2); ++oi) {
+    const int pt = w64 ? 0 : pts_opts[oi];
+    const int fit = w64 ? query_w64_ctas_per_sm(ctx->arch.n_hidden, ctx->prec == NSDF_FP16)
+                        : fp32_ctas_per_sm(ctx->arch.width, pt, ctx->arch.ff_freqs > 0);
     for (int cps = 1; cps <= fit; ++cps) {
       st = grouped_launch(ctx, g, pt, cps, s);             // warm-up (and scratch growth)
       if (st != NSDF_OK) break;
@@ -906,9 +958,11 @@ nsdf_status nsdf_autotune_grouped(nsdf_ctx *ctx, const float *pts, const int64_t
 }
 
 nsdf_status nsdf_set_grouped_config(nsdf_ctx *ctx, int points_per_thread, int ctas_per_sm) {
-  if (!ctx || (points_per_thread != 4 && points_per_thread != 8) || ctas_per_sm < 0)
+  if (!ctx || ctas_per_sm < 0) return NSDF_ERR_INVALID_ARG;
+  const bool one_shape = use_tc16_ff(ctx) || use_w64(ctx);
+  if (points_per_thread != 4 && points_per_thread != 8 && !(one_shape && points_per_thread == 0))
     return NSDF_ERR_INVALID_ARG;
-  ctx->grouped_pt = points_per_thread;
+  if (points_per_thread != 0) ctx->grouped_pt = points_per_thread;
   ctx->grouped_cps = ctas_per_sm;
   return NSDF_OK;
 }

@@ -116,6 +116,11 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   p.out_pts = reinterpret_cast<float4 *>(out_pts);
   p.out_n_sdf = reinterpret_cast<float4 *>(out_n_sdf);
   p.out_hit = out_hit;
+  if (tc16 && query_w64_supported(width, n_hidden, p.skip) && p.ff == 0) {
+    // width-64 tensor-core kernel: no scratch at all
+    const cudaError_t e = launch_query_w64(p, fp16, num_sms, 0, s);
+    return e == cudaSuccess ? NSDF_OK : NSDF_ERR_CUDA;
+  }
   if (tc16 && p.ff > 0) {   // Fourier-feature tensor-core kernel: one slope-bit slab per CTA
     const int grid = query_tc16_ff_grid(n, num_sms);
     if (query_tc16_ff_scratch_bytes(grid) > usable_bytes()) return NSDF_ERR_TOO_LARGE;

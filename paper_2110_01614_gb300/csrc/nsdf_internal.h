@@ -40,6 +40,8 @@ struct NetDevice {
   // Fourier-feature networks hold n_hidden layers here, layer 0 first
   uint16_t *fwd16 = nullptr;  // [n_hidden-1][width(n)][width(k)] = W_l
   uint16_t *bwd16 = nullptr;  // [n_hidden-1][width(k)][width(n)] = W_l^T
+  // BF16 width-64 contexts: the rounding residual W_l - bf16(W_l), in BF16
+  uint16_t *fwd16_lo = nullptr;  // [n_hidden-1][width(n)][width(k)]
   // TMA descriptors of fwd16 / bwd16 (16-bit contexts only)
   CUtensorMap tmap_fwd;
   CUtensorMap tmap_bwd;
@@ -50,6 +52,7 @@ struct NetDevice {
 struct NetPtrs {
   const float *w0, *bias, *fwd_t, *bwd, *wout, *bout;
   const float *ffB, *ff0_t, *ff0;
+  const uint16_t *w16, *w16lo;   // 16-bit hidden weights (and residuals) of the width-64 kernel
 };
 
 // Everything one fused query launch needs (passed by value).
@@ -68,6 +71,7 @@ struct QueryParams {
   // network
   const float *w0, *bias, *fwd_t, *bwd, *wout, *bout;
   const uint16_t *fwd16, *bwd16;
+  const uint16_t *fwd16_lo;  // BF16 width-64 contexts: W_l - bf16(W_l)
   int width, n_hidden, skip;
   float beta;
   int relu;                  // activation: 0 softplus_beta, 1 ReLU
@@ -133,6 +137,15 @@ struct WgradJob {
 int wgrad_splits(int W, int layers, int64_t n_pad, int num_sms);
 bool wgrad_supported(int W);
 cudaError_t launch_wgrad_tc(const WgradJob &job, cudaStream_t s);
+
+// 16-bit tensor-core form for width-64 softplus networks (query_tc16_w64.cu):
+// single-network launches and grouped launches (QueryParams::g_nets > 0, a
+// tile list built with 128-point tiles rounded up to even per network); no
+// per-CTA scratch.  ctas_per_sm <= 0: as many as fit.
+bool query_w64_supported(int width, int n_hidden, int skip);
+int query_w64_ctas_per_sm(int n_hidden, bool fp16);
+cudaError_t launch_query_w64(const QueryParams &p, bool fp16, int num_sms, int ctas_per_sm,
+                             cudaStream_t s);
 
 bool query_tc16_supported(int width, int n_hidden, int skip);
 bool make_tc16_tmaps(NetDevice &net, int width, int n_hidden, bool fp16);

@@ -47,6 +47,7 @@
 #include <cudaTypedefs.h>
 
 #include "nsdf_internal.h"
+#include "softplus.cuh"
 #include "tc_ptx.cuh"
 
 namespace nsdf {
@@ -136,37 +137,6 @@ struct Op {
     }
   }
 };
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;\n" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;\n" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// softplus_beta(z) and its slope sigmoid(beta z) from u = exp(-beta |z|):
-//   softplus_beta(z) = max(z, 0) + log1p(u) / beta,
-//   sigmoid(beta z)  = 1 / (1 + u) for z >= 0, u / (1 + u) otherwise.
-// log1p(u) = u * P(u), P the degree-5 Chebyshev interpolant of log1p(u)/u on
-// [0, 1] printed by gen_log1p_poly.py (relative error < 1e-5).  Two MUFU
-// operations (ex2, rcp) per element; the rest runs on the FMA pipe.
-// neg_bl2e = -beta * log2(e).
-__device__ __forceinline__ void act(float z, float neg_bl2e, float inv_beta, float &h, float &s) {
-  const float u = ex2_approx(fabsf(z) * neg_bl2e);
-  float p = -2.344365580e-02f;
-  p = fmaf(p, u, 1.001397327e-01f);
-  p = fmaf(p, u, -2.090795360e-01f);
-  p = fmaf(p, u, 3.248495807e-01f);
-  p = fmaf(p, u, -4.993146523e-01f);
-  p = fmaf(p, u, 9.999905920e-01f);
-  h = fmaf(u * p, inv_beta, fmaxf(z, 0.0f));
-  const float r = rcp_approx(1.0f + u);
-  s = (z >= 0.0f) ? r : u * r;
-}
 
 // Slopes are written once and read once, up to a tile-time later; all CTAs
 // together keep about 136 MB of them in flight, more than L2 holds.  They are
@@ -417,7 +387,7 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
         float z = __uint_as_float(raw[i]) + comp(bq, u);
         if (AT_SKIP)    // the skip input columns p / sqrt(2), in FP32
           z = fmaf(kInvSqrt2, fmaf(comp(s0, u), e.px, fmaf(comp(s1, u), e.py, comp(s2, u) * e.pz)), z);
-        act(z, e.neg_bl2e, e.inv_beta, hv[u], sv[u]);
+        act_f32(z, e.neg_bl2e, e.inv_beta, hv[u], sv[u]);
         if (LAST) {
           const float wo = comp(wq, u);
           acc.f = fmaf(wo, hv[u], acc.f);
@@ -517,7 +487,7 @@ __device__ __forceinline__ void layer0(const Epi &e) {
       for (int u = 0; u < 4; ++u) {
         const int c = c0 + 4 * q + u;
         const float z = fmaf(w[3 * u], e.px, fmaf(w[3 * u + 1], e.py, fmaf(w[3 * u + 2], e.pz, comp(bq, u))));
-        act(z, e.neg_bl2e, e.inv_beta, hv[u], sv[u]);
+        act_f32(z, e.neg_bl2e, e.inv_beta, hv[u], sv[u]);
         if (FEEDS_SKIP) hv[u] = (c < kNShort) ? hv[u] * kInvSqrt2 : 0.0f;
       }
       if constexpr (kF16) {

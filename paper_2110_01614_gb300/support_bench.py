@@ -7,8 +7,10 @@
   sampled once (as the paper samples a fixed set per shape).
 * penalty: gradient of sum max(0, eps - f)^2 with respect to 1,048,576 vertices.
 * grouped: 16 networks of the 3-64-64-64-1 shape with log-uniform counts in
-  [2k, 400k] (about 1.2M points) in one grouped launch, autotuned, replayed
-  from a CUDA graph; also with a rigid pose per body (nsdf_query_grouped_T).
+  [2k, 400k] (616,218 points) in one grouped launch, autotuned, replayed
+  from a CUDA graph; also with a rigid pose per body (nsdf_query_grouped_T);
+  FP32 kernel and 16-bit tensor-core kernel (BF16, FP16).
+* tiny: 4,096 uniform points through the 3-64-64-64-1 network, one launch.
 * grouped_paper: the same 16-body scene with every body posed and carrying
   its own network of the paper's dragon shape (Fourier features + 8 ReLU
   layers of 256), BF16 tensor cores against the FP32 grouped kernel.
@@ -94,41 +96,64 @@ def bench_penalty(reps=10):
     return {"workload": "penalty_gradient", "vertices": 1 << 20, "ms": ms}
 
 
-def bench_grouped(reps=20):
+def bench_grouped(reps=20, precisions=("fp32", "bf16", "fp16")):
+    """16 networks of the 3-64-64-64-1 shape, log-uniform counts in [2k, 400k]
+    (616,218 points), one autotuned grouped launch replayed from a CUDA graph,
+    with and without a rigid pose per body: the FP32 kernel and the 16-bit
+    tensor-core kernel (split-BF16 / FP16 operands, FP32 accumulation)."""
     counts = synth.grouped_counts()
     offs = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
     total = int(counts.sum())
-    net = NeuralSDF(TINY, NSDF_FP32, n_nets=16)
-    for k in range(16):
-        net.load(synth.geometric_init(TINY, k), net=k)
     P = torch.from_numpy(synth.body_scale_points(total, 5)).cuda()
     O = torch.from_numpy(offs).cuda()
     C = torch.from_numpy(counts.astype(np.int64)).cuda()
-    out, ns = torch.empty_like(P), torch.empty_like(P)
-    pt, cps = tuned_grouped(net, P, O, C, total, 0.002, out, ns)
-    s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        nsdf_query_grouped(net.ctx, P, O, C, total, 0.002, out, ns)
-    s.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=s):
-        nsdf_query_grouped(net.ctx, P, O, C, total, 0.002, out, ns)
-    ms = events_ms(g.replay, reps)
-    # the same scene with every body placed by its own rigid pose (device array)
     Tdev = torch.from_numpy(synth.rigid_transforms(16, seed=77)).cuda()
-    with torch.cuda.stream(s):
-        nsdf_query_grouped_T(net.ctx, P, O, C, total, 0.002, Tdev, out, ns)
-    s.synchronize()
-    gT = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(gT, stream=s):
-        nsdf_query_grouped_T(net.ctx, P, O, C, total, 0.002, Tdev, out, ns)
-    ms_T = events_ms(gT.replay, reps)
-    nsdf_sync_status(net.ctx)
-    net.close()
-    return {"workload": "grouped", "nets": 16, "points": total, "ms": ms,
-            "queries_per_s": total / (ms * 1e-3), "posed_ms": ms_T,
-            "posed_queries_per_s": total / (ms_T * 1e-3), "tile_points_per_thread": pt,
-            "ctas_per_sm": cps, "precision": "fp32"}
+    out, ns = torch.empty_like(P), torch.empty_like(P)
+    res = {"workload": "grouped", "nets": 16, "points": total}
+    for name in precisions:
+        prec = {"fp32": NSDF_FP32, "bf16": NSDF_BF16, "fp16": NSDF_FP16}[name]
+        net = NeuralSDF(TINY, prec, n_nets=16)
+        for k in range(16):
+            net.load(synth.geometric_init(TINY, k), net=k)
+        pt, cps = tuned_grouped(net, P, O, C, total, 0.002, out, ns)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            nsdf_query_grouped(net.ctx, P, O, C, total, 0.002, out, ns)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            nsdf_query_grouped(net.ctx, P, O, C, total, 0.002, out, ns)
+        ms = events_ms(g.replay, reps)
+        with torch.cuda.stream(s):
+            nsdf_query_grouped_T(net.ctx, P, O, C, total, 0.002, Tdev, out, ns)
+        s.synchronize()
+        gT = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gT, stream=s):
+            nsdf_query_grouped_T(net.ctx, P, O, C, total, 0.002, Tdev, out, ns)
+        ms_T = events_ms(gT.replay, reps)
+        nsdf_sync_status(net.ctx)
+        net.close()
+        res[name] = {"ms": ms, "queries_per_s": total / (ms * 1e-3), "posed_ms": ms_T,
+                     "posed_queries_per_s": total / (ms_T * 1e-3),
+                     "tile_points_per_thread": pt, "ctas_per_sm": cps,
+                     "kernel": "query_fp32_kernel" if name == "fp32" else f"query_w64_kernel<{name}>"}
+    return res
+
+
+def bench_tiny(reps=50):
+    """The tiny workload: 4,096 uniform points through the 3-64-64-64-1
+    network, one collision query per launch (latency-bound)."""
+    pts = torch.from_numpy(synth.uniform_cube_points(4096, 1)).cuda()
+    out, ns = torch.empty_like(pts), torch.empty_like(pts)
+    res = {"workload": "tiny", "points": 4096}
+    for name, prec in (("fp32", NSDF_FP32), ("bf16", NSDF_BF16), ("fp16", NSDF_FP16)):
+        net = NeuralSDF(TINY, prec).load(synth.geometric_init(TINY, 0))
+        net.collide(pts, 0.002, out_pts=out, out_n_sdf=ns)
+        ms = events_ms(lambda: net.collide(pts, 0.002, out_pts=out, out_n_sdf=ns), reps)
+        nsdf_sync_status(net.ctx)
+        net.close()
+        res[name] = {"ms": ms, "queries_per_s": 4096 / (ms * 1e-3)}
+    return res
 
 
 def bench_grouped_paper(reps=10):
@@ -292,6 +317,7 @@ def bench_line_support():
     the fitted-body cloth run."""
     out = {}
     for name, fn in (("grouped", lambda: bench_grouped(10)),
+                     ("tiny", lambda: bench_tiny(20)),
                      ("penalty_gradient", lambda: bench_penalty(5)),
                      ("fit_width64_fp32", lambda: bench_fit_pool(10)),
                      ("fit512_bf16", lambda: bench_fit512(10)),
@@ -316,15 +342,15 @@ def bench_fit_pool(steps=10):
 
 
 def main(argv):
-    which = argv or ["fit", "penalty", "grouped", "grouped_paper", "cloth", "paper_arch", "fit512",
-                     "fit_paper", "cloth_fitted"]
+    which = argv or ["fit", "penalty", "grouped", "tiny", "grouped_paper", "cloth", "paper_arch",
+                     "fit512", "fit_paper", "cloth_fitted"]
     torch.cuda.set_device(0)
     for w in which:
         t0 = time.perf_counter()
         r = {"fit": bench_fit, "penalty": bench_penalty, "grouped": bench_grouped,
              "grouped_paper": bench_grouped_paper, "cloth": bench_cloth,
              "paper_arch": bench_paper_arch, "fit512": bench_fit512, "fit_paper": bench_fit_paper,
-             "cloth_fitted": bench_cloth_fitted}[w]()
+             "cloth_fitted": bench_cloth_fitted, "tiny": bench_tiny}[w]()
         r["wall_s"] = time.perf_counter() - t0
         print(json.dumps(r), flush=True)
 

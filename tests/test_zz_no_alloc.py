@@ -27,6 +27,7 @@ def nsdf(nsdf_lib):
 @pytest.mark.parametrize("prec,arch,n", [
     ("bf16", synth.Arch(3, 512, 8, 4, 100.0), 100_003),
     ("fp32", synth.Arch(3, 64, 3, -1, 100.0), 200_001),
+    ("bf16", synth.Arch(3, 64, 3, -1, 100.0), 150_001),
 ])
 def test_noalloc_matches_collide_twice(nsdf, prec, arch, n):
     precision = nsdf.NSDF_BF16 if prec == "bf16" else nsdf.NSDF_FP32
