@@ -107,19 +107,31 @@ __device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo) 
          ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// Named barriers 1 and 2 (one per warpgroup), with immediate IDs: a barrier
+// ID in a register makes the compiler reserve all 16 barriers of the CTA,
+// which limits an SM to one CTA.
 __device__ __forceinline__ void wg_bar(int wg) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(1 + wg), "r"(128) : "memory");
+  if (wg == 0) asm volatile("bar.sync 1, 128;\n" ::: "memory");
+  else asm volatile("bar.sync 2, 128;\n" ::: "memory");
 }
 // Barrier of the warpgroup that also ANDs a predicate over its 128 threads,
 // so that all of them take the same path after a bounded wait.
 __device__ __forceinline__ bool wg_all(int wg, bool v) {
   uint32_t res;
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred p, %2, 128, p;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(res)
-      : "r"((uint32_t)v), "r"(1 + wg)
-      : "memory");
+  if (wg == 0)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred p, 1, 128, p;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(res)
+        : "r"((uint32_t)v)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred p, 2, 128, p;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(res)
+        : "r"((uint32_t)v)
+        : "memory");
   return res != 0;
 }
 
@@ -460,20 +472,28 @@ int launch_smem(int L, int num_sms_unused) {
   return need > cap ? need : cap;
 }
 
+// CTAs per SM: as many as the SM's registers, shared memory and TMEM
+// columns hold (computed from the device's limits and the kernel's register
+// count).
 template <bool kF16>
 int resident_ctas(int L) {
   const int smem = launch_smem<kF16>(L, 0);
-  if (cudaFuncSetAttribute(query_w64_kernel<kF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem) != cudaSuccess)
-    return 0;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, query_w64_kernel<kF16>, kThreads,
-                                                    smem) != cudaSuccess) {
+  int dev = 0, smem_sm = 0, regs_sm = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, query_w64_kernel<kF16>) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  const int fit = 512 / cta_cols(L);
-  return per_sm < fit ? per_sm : fit;
+  const int by_smem = smem_sm / (smem + 1024);                 // 1 KB reserved per CTA
+  const int by_regs = regs_sm / (fa.numRegs * kThreads);
+  int fit = 512 / cta_cols(L);
+  if (by_smem < fit) fit = by_smem;
+  if (by_regs < fit) fit = by_regs;
+  return fit;
 }
 
 template <bool kF16>

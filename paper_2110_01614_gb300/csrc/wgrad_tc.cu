@@ -10,7 +10,8 @@
 // swizzle) is one K x MN block of either operand.
 //
 // Work units: an output tile of 128 rows (n) x 256 columns (k) of one layer
-// and one of S contiguous ranges of the points (split K).  A persistent CTA
+// and one of S contiguous ranges of the points (split K), ordered range by
+// range.  A persistent CTA
 // per SM walks its units; per unit, 64-point steps stream through a 4-stage
 // ring (A: 2 boxes of 64 x 64 = 16 KB, B: 4 boxes = 32 KB), one thread issues
 // 4 tcgen05.mma (M=128, N=256, K=16; 16-bit x 16-bit -> FP32) per step into
@@ -139,9 +140,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     atomicExch(prm.err, kDevTimeout);
     *abort_flag = 1;
   };
-  // unit -> (product, tile row, tile column, first and end step)
+  // unit -> (product, tile row, tile column, first and end step).  Units run
+  // tile-minor: the CTAs working at the same time share one range of points,
+  // so each 64-point box of D and H comes from DRAM once and from L2 for the
+  // other tiles of its layer.
   auto decode = [&](int64_t u, int &li, int &mt, int &nt, int64_t &kb, int64_t &ke) {
-    const int t = (int)(u / prm.S), s = (int)(u % prm.S);
+    const int t = (int)(u % tiles), s = (int)(u / tiles);
     li = t / (mt_n * nt_n);
     const int rem = t % (mt_n * nt_n);
     mt = rem / nt_n;
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       acc_phase[b] ^= 1u;
       tc_fence_after();
-      const int s = (int)(u % prm.S);
+      const int s = (int)(u / tiles);
       float *dst = prm.ws + (((size_t)li * prm.S + s) * W + (size_t)mt * kTM + row) * W +
                    (size_t)nt * kTN;
       const uint32_t t_row = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTN);
