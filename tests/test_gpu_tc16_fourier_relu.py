@@ -24,6 +24,15 @@ Two references, because a ReLU slope is a decision taken by floating point:
   |z| below that, an extra flip at a few percent of the points of the
   8-layer network.  So the normal must agree within 1e-3 rad at 90% of the
   points and within 1e-2 rad at 95% (measured: 93-99% and 96-99.5%).
+  No fixed margin on |z| makes a point safe from such flips on the 8-layer
+  network: one feature or activation rounded to the other 16-bit neighbour
+  shifts the next layer's z, which moves more roundings, so the shifts grow
+  with depth (an FP64 emulation with kernel-sized feature errors: up to
+  2e-3 at layer 0 and 3e-2 at layer 7 in BF16, 5e-4 to 5e-3 in FP16).
+  Point-by-point agreement is therefore tested on a network built so that
+  no rounding is ambiguous (the element-wise test at the end of this file):
+  there f must match the rounded oracle to FP32 rounding and the normal to
+  1e-5 rad at every point.
 * ``oracle.mlp`` is exact.  f is continuous through the ReLU kinks, so its
   error is bounded by the rounding alone: the rounded oracle is within 16 u
   of it (tests/test_oracle_rounded.py), so the kernel must be within 24 u.
@@ -425,3 +434,109 @@ def test_host_buffers_equal_device_buffers(nsdf):
     s.close()
     assert torch.equal(h_out, d_out.cpu()) and torch.equal(h_ns, d_ns.cpu())
     assert torch.equal(h_hit, d_hit.cpu())
+
+
+# ------------------------------------------------------------------ element-wise
+# A network of the paper's shape on which the kernel and the rounded oracle
+# take identical rounding decisions, so that they must agree at every point:
+#   * frequencies B in {-2, 0, 2} and points on the grid (Z/4)^3: every phase
+#     2 pi b.p is a multiple of pi, so the kernel's features (FMA phase,
+#     integer part removed, sine and cosine of a zero remainder) are exactly
+#     0 and +-1, and the oracle's are within 1e-16 of them;
+#   * W_0 with four entries +-1/2 per row and bias 1/4: every pre-activation
+#     of layer 0 is exactly representable in 16 bits, so the oracle's 1e-16
+#     cannot change its rounding;
+#   * sparse dyadic hidden weights, checked below so that every sum the
+#     kernel forms in FP32 (forward and reverse products, any order) is
+#     exact: both sides then round the same values, ties included.
+def exact_ff_network(L, fmt, grid_pts, seed0=0):
+    arch = synth.Arch(3, 256, L, -1, 100.0, "relu", 128)
+    m, W = 128, 256
+
+    def lowbit(x):
+        """Value of the lowest set bit of each dyadic float64 value; inf for 0."""
+        mant, ex = np.frexp(np.abs(x))
+        q = np.round(mant * 2.0 ** 53).astype(np.int64)
+        return np.where(q != 0, (q & -q).astype(np.float64) * 2.0 ** (ex - 53.0), np.inf)
+
+    def fp32_exact(x, Wl, bias):
+        """Every partial sum of x @ Wl.T + bias exact in FP32, in any order:
+        all terms are multiples of their smallest lowest bit, and the sum of
+        their magnitudes stays below 2^23 of it."""
+        rows, cols = np.nonzero(Wl)
+        lb_b = lowbit(bias)
+        lb = np.broadcast_to(lb_b, (x.shape[0], Wl.shape[0])).copy()
+        if rows.size:
+            tl = lowbit(x[:, cols] * Wl[rows, cols])
+            starts = np.searchsorted(rows, np.arange(Wl.shape[0]))
+            has = np.bincount(rows, minlength=Wl.shape[0]) > 0
+            red = np.minimum.reduceat(tl, np.minimum(starts, rows.size - 1), axis=1)
+            lb[:, has] = np.minimum(lb[:, has], red[:, has])
+        tot = np.abs(x) @ np.abs(Wl).T + np.abs(bias)[None, :]
+        return bool(np.all((tot == 0) | (tot < 2.0 ** 23 * lb)))
+
+    p = grid_pts[:, :3].astype(np.float64)
+    for seed in range(seed0, seed0 + 40):
+        s = synth.Stream(seed, tag=777)
+        B = 2.0 * (s.u64(m * 3) % np.uint64(3)).astype(np.float64).reshape(m, 3) - 2.0
+        layers = []
+        W0 = np.zeros((W, 2 * m))
+        for i in range(W):
+            cols = (s.u64(4) % np.uint64(2 * m)).astype(np.int64)
+            W0[i, cols] = 0.5 * (2.0 * (s.u64(4) % np.uint64(2)).astype(np.float64) - 1.0)
+        layers.append((W0, np.full(W, 0.25)))
+        for _ in range(1, L):
+            Wl = np.zeros((W, W))
+            for i in range(W):
+                cols = (s.u64(3) % np.uint64(W)).astype(np.int64)
+                mag = 2.0 ** -(1 + (s.u64(3) % np.uint64(2)).astype(np.float64))
+                Wl[i, cols] = mag * (2.0 * (s.u64(3) % np.uint64(2)).astype(np.float64) - 1.0)
+            bl = 0.125 * ((s.u64(W) % np.uint64(3)).astype(np.float64) - 1.0)
+            layers.append((Wl, bl))
+        wout = 2.0 ** -4 * (2.0 * (s.u64(W) % np.uint64(2)).astype(np.float64) - 1.0)
+        layers.append((wout[None, :], np.zeros(1)))
+        # forward and reverse with the 16-bit rounding points, checking exactness
+        phase = 2.0 * np.pi * (p @ B.T)
+        x = np.concatenate([np.round(np.sin(phase)), np.round(np.cos(phase))], axis=1)
+        z0 = x @ W0.T + 0.25
+        ok = np.array_equal(rounded.round16(z0, fmt), z0) and np.abs(z0).min() >= 0.25
+        masks, xs = [], []
+        for l in range(L):
+            Wr = rounded.round16(layers[l][0], fmt)
+            ok = ok and np.array_equal(Wr, layers[l][0]) and fp32_exact(x, Wr, layers[l][1])
+            z = x @ Wr.T + layers[l][1]
+            masks.append(z > 0)
+            xs.append(x)
+            if l == L - 1:      # the output unit: an FP32 dot of the unrounded h
+                ok = ok and fp32_exact(np.maximum(z, 0.0), wout[None, :], np.zeros(1))
+            x = rounded.round16(np.maximum(z, 0.0), fmt)
+        delta = rounded.round16(np.where(masks[L - 1], wout[None, :], 0.0), fmt)
+        for l in range(L - 1, 0, -1):
+            ok = ok and fp32_exact(delta, layers[l][0].T, np.zeros(W))
+            delta = rounded.round16(np.where(masks[l - 1], delta @ layers[l][0], 0.0), fmt)
+        ok = ok and fp32_exact(delta, layers[0][0].T, np.zeros(2 * m))
+        if ok:
+            parts = [B.ravel()]
+            for Wl, bl in layers:
+                parts += [Wl.ravel(), bl.ravel()]
+            return arch, np.concatenate(parts).astype(np.float32)
+    raise AssertionError("no exact network found")
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+@pytest.mark.parametrize("L", [4, 8])
+def test_elementwise_on_a_network_without_rounding_ambiguity(nsdf, fmt, L):
+    g = np.arange(-4, 5) / 4.0
+    grid = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    pts = np.zeros((len(grid), 4), dtype=np.float32)
+    pts[:, :3] = grid
+    arch, blob = exact_ff_network(L, fmt, pts)
+    out, ns, hit = collide_gpu(nsdf, fmt, arch, blob, pts)
+    f_r, g_r, _ = rounded.query_ff_relu(blob, arch, pts[:, :3].astype(np.float64), fmt)
+    f = ns[:, 3].astype(np.float64)
+    assert np.abs(f - f_r).max() <= 1e-6 * max(1.0, np.abs(f_r).max())
+    nrm = np.linalg.norm(g_r, axis=1)
+    assert nrm.min() > 0
+    ang = normal_angle(g_r / nrm[:, None], ns[:, :3])
+    print(fmt, L, "max angle", float(ang.max()), "f range", float(f_r.min()), float(f_r.max()))
+    assert ang.max() <= 1e-5
