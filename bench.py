@@ -43,12 +43,12 @@ FLOP_PER_QUERY = 2 * MAC_PER_QUERY
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the tensor-core kernel on this workload, from one ncu capture, keyed by the
-# SHA-256 of the kernel's code (query_tc16.cu and its inline-PTX header
-# tc_ptx.cuh, comments and blank lines removed) it was taken on; reported
+# SHA-256 of the kernel's code (query_tc16.cu and its headers tc_ptx.cuh and
+# softplus.cuh, comments and blank lines removed) it was taken on; reported
 # only while that code is unchanged.
 TRAFFIC_CAPTURE = {
-    "code_sha256": "43ac0e3b56082eed4e78a384b4f53f628f4a1c2fa00e1bfecb1901a45b235664",
-    "bytes_per_launch": 3.984380e9 + 4.856618e9,
+    "code_sha256": "2bc4adad8764c47ab635987a3d5a7343a1872f7a096418258943e63f7bbc2b47",
+    "bytes_per_launch": 3.64e9 + 4.58e9,
 }
 
 
@@ -64,7 +64,7 @@ def code_sha256(text):
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
-KERNEL_SOURCES = ("query_tc16.cu", "tc_ptx.cuh")
+KERNEL_SOURCES = ("query_tc16.cu", "tc_ptx.cuh", "softplus.cuh")
 
 
 def kernel_code_sha256():
@@ -361,6 +361,13 @@ def run_gpu(args):
         other[name] = {"value": n / statistics.mean(d), "unit": "queries/s",
                        "ms_per_step": 1e3 * statistics.mean(d),
                        "ns": out_ns.cpu().numpy(), "hit": out_hit.cpu().numpy().astype(bool)}
+        if name == "fp32":
+            # the FP32 form against the measured FP32 FMA throughput of this GPU
+            fma = nsdf.nsdf_debug_fp32_fma_peak()
+            tf = FLOP_PER_QUERY * n / statistics.mean(d) / 1e12
+            other[name]["roofline"] = {"bound": "fp32 fma", "achieved": tf, "peak": fma,
+                                       "unit": "TFLOP/s", "frac": tf / fma,
+                                       "peak_source": "measured (nsdf_debug_fp32_fma_peak)"}
         ctx.close()
 
     # --- the paper's own network shapes (Sec. 4.3) on the same points, BF16 tensor cores ---
@@ -420,7 +427,8 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": n * 16,
                 "d2h_bytes_per_step": n * (16 + 16 + 1)},
         "forms": {name: {"value": o["value"], "unit": "queries/s", "ms_per_step": o["ms_per_step"],
-                         "bf16_speedup_over_this": value / o["value"]}
+                         "bf16_speedup_over_this": value / o["value"],
+                         **({"roofline": o["roofline"]} if "roofline" in o else {})}
                   for name, o in other.items()},
         "clocks": clk,
     }

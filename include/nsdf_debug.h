@@ -37,6 +37,14 @@ nsdf_status nsdf_debug_inject(nsdf_ctx *ctx, int drop_load, long long wait_budge
  */
 nsdf_status nsdf_debug_noalloc_limit(size_t bytes);
 
+/*
+ * Measures the FP32 FMA throughput of the current GPU (the peak against
+ * which the FP32 form's arithmetic is reported): independent FMA chains on
+ * every SM, timed with CUDA events on `stream`, best of three launches;
+ * writes TFLOP/s (2 FLOP per FMA) to *tflops.  Synchronises `stream`.
+ */
+nsdf_status nsdf_debug_fp32_fma_peak(double *tflops, nsdf_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

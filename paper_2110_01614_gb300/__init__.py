@@ -28,7 +28,7 @@ __all__ = [
     "nsdf_query_grouped_T", "nsdf_l1_grad",
     "nsdf_autotune_grouped", "nsdf_set_grouped_config",
     "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status", "nsdf_debug_inject",
-    "nsdf_debug_noalloc_limit",
+    "nsdf_debug_noalloc_limit", "nsdf_debug_fp32_fma_peak",
     "nsdf_status_string", "NeuralSDF", "library",
 ]
 
@@ -208,6 +208,14 @@ def nsdf_debug_inject(ctx, drop_load=-1, wait_budget_cycles=4_000_000_000):
 def nsdf_debug_noalloc_limit(nbytes):
     """Test-only: cap the bytes of nsdf_collide_noalloc's fixed array (0 = all)."""
     _check(library().nsdf_debug_noalloc_limit(int(nbytes)), "nsdf_debug_noalloc_limit")
+
+
+def nsdf_debug_fp32_fma_peak(stream=None):
+    """Measured FP32 FMA throughput of the current GPU, TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(library().nsdf_debug_fp32_fma_peak(ctypes.byref(v), _stream(stream)),
+           "nsdf_debug_fp32_fma_peak")
+    return v.value
 
 
 def nsdf_sync_status(ctx, stream=None):
