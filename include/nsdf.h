@@ -285,6 +285,36 @@ nsdf_status nsdf_set_grouped_config(nsdf_ctx *ctx, int points_per_thread,
                                     int ctas_per_sm);
 
 /*
+ * Voxel SDF baseline, the comparison system of Sec. 4.3 (Table 1): the
+ * signed distance sampled on a regular grid of n^3 nodes over the box
+ * [lo, hi] (lo, hi: 3 floats each, HOST memory), node (i, j, k) at
+ * lo + (i, j, k) (hi - lo) / (n - 1) stored at grid[i + n (j + n k)]
+ * (float, DEVICE, n^3 values; n = 256 is 64 MB).
+ *
+ * nsdf_voxel_build fills the grid with the exact signed distance of every
+ * node to a watertight mesh (the brute force of nsdf_mesh_sdf; same mesh
+ * arguments, DEVICE pointers).  n in [2, 2048].
+ *
+ * nsdf_voxel_collide answers the collision query of nsdf_collide from the
+ * grid: sdf by trilinear interpolation of the node values, normal = the
+ * normalised gradient of that interpolant (Eq. 2 applied to it), hit =
+ * sdf < eps and the contact point of Eq. 3.  A point outside the box takes
+ * the value at its nearest point of the box plus its distance to the box,
+ * and that distance's gradient is added to the normal's.  pts, out_pts,
+ * out_n_sdf (float4, 16-byte aligned) and out_hit are DEVICE memory (host
+ * memory: NSDF_ERR_INVALID_ARG); out_n_sdf and out_hit nullable; out_pts
+ * may alias pts.  Asynchronous on `stream`.
+ */
+nsdf_status nsdf_voxel_build(const float *verts, int64_t n_verts,
+                             const int32_t *faces, int64_t n_faces, int n,
+                             const float *lo, const float *hi, float *grid,
+                             nsdf_stream stream);
+nsdf_status nsdf_voxel_collide(const float *grid, int n, const float *lo,
+                               const float *hi, const float *pts, int64_t n_pts,
+                               float eps, float *out_pts, float *out_n_sdf,
+                               uint8_t *out_hit, nsdf_stream stream);
+
+/*
  * Ground-truth signed distance to a watertight triangle mesh by brute force
  * (the targets of Sec. 3.1): out_sdf[i] = +-min_t dist(p_i, triangle t),
  * negative where the generalized winding number exceeds 1/2 (interior

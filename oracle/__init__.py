@@ -21,10 +21,13 @@ Contents, each function citing the passage of the paper it follows:
   decisions are taken in the precision of the 16-bit kernels.
 * ``cloth`` - one explicit Verlet step of a mass-spring quad cloth followed
   by the collision solve (Sec. 4.1).
+* ``voxel`` - the voxel SDF baseline of Sec. 4.3 (Table 1): trilinear
+  interpolation of a grid of signed distances, its gradient and the same
+  collision query.
 
 Parity status: every function here is pinned by closed forms, brute force or
 finite differences in ``tests/test_oracle_*.py``; the paper prints no worked
 numerical example, so nothing is pinned to a printed value.
 """
 
-from . import mlp, mesh, cloth, rounded  # noqa: F401
+from . import mlp, mesh, cloth, rounded, voxel  # noqa: F401

@@ -28,7 +28,8 @@ __all__ = [
     "nsdf_query_grouped_T", "nsdf_l1_grad",
     "nsdf_autotune_grouped", "nsdf_set_grouped_config",
     "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status", "nsdf_debug_inject",
-    "nsdf_debug_noalloc_limit", "nsdf_debug_fp32_fma_peak",
+    "nsdf_debug_noalloc_limit", "nsdf_debug_fp32_fma_peak", "nsdf_voxel_build",
+    "nsdf_voxel_collide",
     "nsdf_status_string", "NeuralSDF", "library",
 ]
 
@@ -208,6 +209,31 @@ def nsdf_debug_inject(ctx, drop_load=-1, wait_budget_cycles=4_000_000_000):
 def nsdf_debug_noalloc_limit(nbytes):
     """Test-only: cap the bytes of nsdf_collide_noalloc's fixed array (0 = all)."""
     _check(library().nsdf_debug_noalloc_limit(int(nbytes)), "nsdf_debug_noalloc_limit")
+
+
+def _box(lo, hi):
+    a = (ctypes.c_float * 3)(*[float(v) for v in lo])
+    b = (ctypes.c_float * 3)(*[float(v) for v in hi])
+    return a, b
+
+
+def nsdf_voxel_build(verts, faces, n, lo, hi, grid, stream=None):
+    """Fill grid (device float [n^3]) with the exact signed distance of every node."""
+    a, b = _box(lo, hi)
+    _check(library().nsdf_voxel_build(_ptr(verts), verts.shape[0], _ptr(faces), faces.shape[0],
+                                      int(n), ctypes.cast(a, ctypes.c_void_p),
+                                      ctypes.cast(b, ctypes.c_void_p), _ptr(grid),
+                                      _stream(stream)), "nsdf_voxel_build")
+
+
+def nsdf_voxel_collide(grid, n, lo, hi, pts, eps, out_pts, out_n_sdf=None, out_hit=None,
+                       stream=None):
+    """The collision query answered from a voxel grid (trilinear interpolation)."""
+    a, b = _box(lo, hi)
+    _check(library().nsdf_voxel_collide(_ptr(grid), int(n), ctypes.cast(a, ctypes.c_void_p),
+                                        ctypes.cast(b, ctypes.c_void_p), _ptr(pts), pts.shape[0],
+                                        float(eps), _ptr(out_pts), _ptr(out_n_sdf), _ptr(out_hit),
+                                        _stream(stream)), "nsdf_voxel_collide")
 
 
 def nsdf_debug_fp32_fma_peak(stream=None):

@@ -65,6 +65,9 @@ SIGNATURES = {
                               ctypes.c_float, _P]),
     "nsdf_sync_status": (_ST, [_P, _P]),
     "nsdf_status_string": (ctypes.c_char_p, [_ST]),
+    "nsdf_voxel_build": (_ST, [_P, _I64, _P, _I64, ctypes.c_int, _P, _P, _P, _P]),
+    "nsdf_voxel_collide": (_ST, [_P, ctypes.c_int, _P, _P, _P, _I64, ctypes.c_float, _P, _P, _P,
+                                 _P]),
     "nsdf_debug_inject": (_ST, [_P, ctypes.c_int, ctypes.c_longlong]),
     "nsdf_debug_noalloc_limit": (_ST, [ctypes.c_size_t]),
     "nsdf_debug_fp32_fma_peak": (_ST, [ctypes.POINTER(ctypes.c_double), _P]),

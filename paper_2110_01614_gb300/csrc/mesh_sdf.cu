@@ -9,7 +9,8 @@
 // Omega_t from the Van Oosterom-Strackee formula.
 //
 // Triangles stream through shared memory in chunks; each thread owns one
-// point.  w is accumulated in FP32; for points where that is not decisive
+// point: an explicit float4, or node (i, j, k) of a regular grid (i fastest)
+// when the voxel baseline builds its grid.  w is accumulated in FP32; for points where that is not decisive
 // (|w - 1/2| < 0.25, or distance < 1e-3 where one nearby triangle's solid
 // angle is ill-conditioned) the warp recomputes w in FP64, all 32 lanes
 // splitting the triangles of one such point at a time.
@@ -119,17 +120,34 @@ __device__ __forceinline__ T solid_angle(V3<T> p, V3<T> a, V3<T> b, V3<T> c) {
   return T(2) * atan2(num, den);
 }
 
+// Points of the implicit grid: node (i, j, k) at lo + (i, j, k) * h, index
+// i + N (j + N k).
+struct GridPts {
+  int n;
+  float lo[3], h[3];
+};
+
 __global__ void __launch_bounds__(kThreads) mesh_sdf_kernel(const float *__restrict__ V, int64_t nv,
                                                             const int32_t *__restrict__ F,
                                                             int64_t nf, const float4 *__restrict__ pts,
-                                                            int64_t n, float *__restrict__ out) {
+                                                            int64_t n, float *__restrict__ out,
+                                                            const GridPts grid) {
   extern __shared__ float4 smem4[];
   TriChunk &tc = *reinterpret_cast<TriChunk *>(smem4);
   __shared__ double wacc[kThreads / 32][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (idx < n) p4 = pts[idx];
+  if (idx < n) {
+    if (pts) {
+      p4 = pts[idx];
+    } else {
+      const int64_t N = grid.n;
+      p4.x = grid.lo[0] + grid.h[0] * (float)(idx % N);
+      p4.y = grid.lo[1] + grid.h[1] * (float)((idx / N) % N);
+      p4.z = grid.lo[2] + grid.h[2] * (float)(idx / (N * N));
+    }
+  }
   const V3<float> p = {p4.x, p4.y, p4.z};
   float best = 3.4e38f, wsum = 0.f;
   for (int64_t f0 = 0; f0 < nf; f0 += kChunk) {
@@ -184,6 +202,28 @@ __global__ void __launch_bounds__(kThreads) mesh_sdf_kernel(const float *__restr
 }
 
 }  // namespace
+
+cudaError_t launch_mesh_sdf(const float *verts, int64_t n_verts, const int32_t *faces,
+                            int64_t n_faces, const float4 *pts, int64_t n, float *out, int grid_n,
+                            const float *lo, const float *h, cudaStream_t s) {
+  const size_t smem = sizeof(TriChunk);
+  cudaError_t e = cudaFuncSetAttribute(mesh_sdf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  GridPts g{};
+  if (!pts) {
+    g.n = grid_n;
+    for (int c = 0; c < 3; ++c) {
+      g.lo[c] = lo[c];
+      g.h[c] = h[c];
+    }
+  }
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  mesh_sdf_kernel<<<(unsigned)blocks, kThreads, smem, s>>>(verts, n_verts, faces, n_faces, pts, n,
+                                                          out, g);
+  return cudaGetLastError();
+}
+
 }  // namespace nsdf
 
 extern "C" nsdf_status nsdf_mesh_sdf(const float *verts, int64_t n_verts, const int32_t *faces,
@@ -194,12 +234,8 @@ extern "C" nsdf_status nsdf_mesh_sdf(const float *verts, int64_t n_verts, const 
   if (!verts || !faces || !pts || !out_sdf || n_faces == 0 || n_verts < 3) return NSDF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(pts) & 15u) != 0) return NSDF_ERR_MISALIGNED;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t smem = sizeof(nsdf::TriChunk);
-  cudaError_t e = cudaFuncSetAttribute(nsdf::mesh_sdf_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return NSDF_ERR_CUDA;
-  const int64_t blocks = (n + nsdf::kThreads - 1) / nsdf::kThreads;
-  nsdf::mesh_sdf_kernel<<<(unsigned)blocks, nsdf::kThreads, smem, s>>>(
-      verts, n_verts, faces, n_faces, reinterpret_cast<const float4 *>(pts), n, out_sdf);
-  return cudaGetLastError() == cudaSuccess ? NSDF_OK : NSDF_ERR_CUDA;
+  return nsdf::launch_mesh_sdf(verts, n_verts, faces, n_faces, reinterpret_cast<const float4 *>(pts),
+                               n, out_sdf, 0, nullptr, nullptr, s) == cudaSuccess
+             ? NSDF_OK
+             : NSDF_ERR_CUDA;
 }

@@ -147,6 +147,13 @@ int query_w64_ctas_per_sm(int n_hidden, bool fp16);
 cudaError_t launch_query_w64(const QueryParams &p, bool fp16, int num_sms, int ctas_per_sm,
                              cudaStream_t s);
 
+// Brute-force mesh SDF (mesh_sdf.cu) of n explicit points, or, with
+// pts == nullptr, of the n = grid_n^3 nodes lo + (i, j, k) h of a regular
+// grid (index i + grid_n (j + grid_n k)).
+cudaError_t launch_mesh_sdf(const float *verts, int64_t n_verts, const int32_t *faces,
+                            int64_t n_faces, const float4 *pts, int64_t n, float *out, int grid_n,
+                            const float *lo, const float *h, cudaStream_t s);
+
 bool query_tc16_supported(int width, int n_hidden, int skip);
 bool make_tc16_tmaps(NetDevice &net, int width, int n_hidden, bool fp16);
 cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bool fp16,

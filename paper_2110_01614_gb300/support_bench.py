@@ -35,6 +35,9 @@
   icosphere represented by a body-scale network fitted to it (BF16 tensor-core
   fitting), per-step time in BF16 / FP16 / FP32 and of the brute-force mesh
   SDF of every vertex.
+* voxel: the voxel SDF baseline (Sec. 4.3, Table 1) at N = 256 against the
+  fitted body-scale network: build time, memory, query time for 1M points
+  and error against the exact signed distance near the surface.
 
 Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped grouped_paper cloth
                                                       paper_arch fit512 fit_paper]
@@ -50,8 +53,8 @@ import torch
 
 import synth
 
-from . import (NSDF_BF16, NSDF_FP16, NSDF_FP32, NeuralSDF, nsdf_query_grouped, nsdf_query_grouped_T,
-               nsdf_sync_status)
+from . import (NSDF_BF16, NSDF_FP16, NSDF_FP32, NeuralSDF, nsdf_mesh_sdf, nsdf_query_grouped,
+               nsdf_query_grouped_T, nsdf_sync_status)
 from .cloth_sim import ClothSim, mesh_reference_step_ms
 from .fit import MeshFit, penalty_gradient
 from .tune import tuned_grouped
@@ -278,23 +281,30 @@ def bench_fit_paper(steps=20):
             "loss_first": losses[0], "loss_last": losses[-1]}
 
 
-def bench_cloth_fitted(steps=100, fit_steps=300, fp32_steps=100):
-    """Cloth of 1024 x 1024 vertices dropped for `steps` explicit steps onto
-    the displaced icosphere (20,480 triangles) represented by a network of the
-    body-scale shape (3-512x8-1, skip at L4) fitted to it on the BF16
-    tensor-core path (L1 loss, pool of 1,048,576 points, `fit_steps` batches
-    of 250,000); per-step time of Verlet + collision solve in BF16, FP16 and
-    FP32, and of the exact brute-force mesh SDF of every vertex."""
+def fit_body(fit_steps=300):
+    """The body-scale network (3-512x8-1, skip at L4) fitted to the displaced
+    icosphere (20,480 triangles) on the BF16 tensor-core path: L1 loss, pool
+    of 1,048,576 points, `fit_steps` batches of 250,000.  Returns the FP32
+    blob and the fitting record."""
     from .fit import MeshFitTC
     V, F = synth.displaced_icosphere(level=5, seed=7)
     fit = MeshFitTC(BODY, V, F, precision=NSDF_BF16, pool_points=1 << 20, batch=250_000)
     losses, fit_s = fit.run(fit_steps)
     blob = fit.weights()
     fit.close()
+    return blob, {"fit_steps": fit_steps, "fit_s_per_step": fit_s, "fit_l1_first": losses[0],
+                  "fit_l1_last": losses[-1]}
+
+
+def bench_cloth_fitted(steps=100, fit_steps=300, fp32_steps=100, fitted=None):
+    """Cloth of 1024 x 1024 vertices dropped for `steps` explicit steps onto
+    the displaced icosphere represented by the body-scale network fitted to
+    it (fit_body); per-step time of Verlet + collision solve in BF16, FP16 and
+    FP32, and of the exact brute-force mesh SDF of every vertex."""
+    V, F = synth.displaced_icosphere(level=5, seed=7)
+    blob, info = fitted if fitted is not None else fit_body(fit_steps)
     res = {"workload": "cloth_fitted_body", "grid": "1024x1024", "steps": steps,
-           "body": "3-512x8-1 (skip L4) fitted to the displaced icosphere",
-           "fit_steps": fit_steps, "fit_s_per_step": fit_s, "fit_l1_first": losses[0],
-           "fit_l1_last": losses[-1]}
+           "body": "3-512x8-1 (skip L4) fitted to the displaced icosphere", **info}
     for name, prec, k in (("bf16", NSDF_BF16, steps), ("fp16", NSDF_FP16, steps),
                           ("fp32", NSDF_FP32, fp32_steps)):
         body = NeuralSDF(BODY, prec).load(blob)
@@ -311,6 +321,49 @@ def bench_cloth_fitted(steps=100, fit_steps=300, fp32_steps=100):
     return res
 
 
+def bench_voxel(fitted=None, n=256, reps=20):
+    """The voxel SDF baseline of Sec. 4.3 (Table 1) on this build's shape: an
+    n^3 grid of exact signed distances to the displaced icosphere over
+    [-1, 1]^3 against the fitted body-scale network (BF16): build time,
+    memory, collision-query time for 1,048,576 points, and |f - d| against
+    the exact signed distance d at 262,144 points (80% near the surface)."""
+    from . import nsdf_voxel_build, nsdf_voxel_collide
+    V, F = synth.displaced_icosphere(level=5, seed=7)
+    blob, _ = fitted if fitted is not None else fit_body()
+    Vd = torch.from_numpy(V.astype(np.float32)).cuda().contiguous()
+    Fd = torch.from_numpy(F.astype(np.int32)).cuda().contiguous()
+    lo, hi = -np.ones(3), np.ones(3)
+    grid = torch.empty(n ** 3, device="cuda")
+    build_ms = events_ms(lambda: nsdf_voxel_build(Vd, Fd, n, lo, hi, grid), 1)
+    pts = torch.from_numpy(synth.body_scale_points(1 << 20, 1)).cuda()
+    out, ns = torch.empty_like(pts), torch.empty_like(pts)
+    vox_ms = events_ms(lambda: nsdf_voxel_collide(grid, n, lo, hi, pts, 0.002, out, ns), reps)
+    net = NeuralSDF(BODY, NSDF_BF16).load(blob)
+    net_ms = events_ms(lambda: net.collide(pts, 0.002, out_pts=out, out_n_sdf=ns), reps)
+    # accuracy against the exact signed distance near the surface
+    P = torch.from_numpy(synth.training_points(V, F, 1 << 18, 4242)).cuda()
+    d = torch.empty(P.shape[0], device="cuda")
+    nsdf_mesh_sdf(Vd, Fd, P, d)
+    o2, n2 = torch.empty_like(P), torch.empty_like(P)
+    nsdf_voxel_collide(grid, n, lo, hi, P, 0.002, o2, n2)
+    ev = (n2[:, 3] - d).abs()
+    net.collide(P, 0.002, out_pts=o2, out_n_sdf=n2)
+    en = (n2[:, 3] - d).abs()
+    nsdf_sync_status(net.ctx)
+    net.close()
+    params = synth.n_params(BODY)
+    return {"workload": "voxel_vs_network", "grid_n": n, "grid_mb": n ** 3 * 4 / 2 ** 20,
+            "grid_build_ms": build_ms, "network_params": params,
+            "network_mb_fp32": params * 4 / 2 ** 20, "network_mb_16bit_copies": params * 2 / 2 ** 20,
+            "query_1M_ms": {"voxel": vox_ms, "network_bf16": net_ms},
+            "abs_error_vs_exact": {
+                "points": int(P.shape[0]),
+                "voxel": {"mean": float(ev.mean()), "p99": float(ev.quantile(0.99)),
+                          "max": float(ev.max())},
+                "network_bf16": {"mean": float(en.mean()), "p99": float(en.quantile(0.99)),
+                                 "max": float(en.max())}}}
+
+
 def bench_line_support():
     """The support workloads in one bounded pass (about a minute), for the
     benchmark line: grouped launch, penalty gradient, the fitting steps and
@@ -320,12 +373,18 @@ def bench_line_support():
                      ("tiny", lambda: bench_tiny(20)),
                      ("penalty_gradient", lambda: bench_penalty(5)),
                      ("fit_width64_fp32", lambda: bench_fit_pool(10)),
-                     ("fit512_bf16", lambda: bench_fit512(10)),
-                     ("cloth", bench_cloth_fitted)):
+                     ("fit512_bf16", lambda: bench_fit512(10))):
         t0 = time.perf_counter()
         r = fn()
         r["wall_s"] = time.perf_counter() - t0
         out[name] = r
+    t0 = time.perf_counter()
+    fitted = fit_body()
+    for name, fn in (("cloth", bench_cloth_fitted), ("voxel", bench_voxel)):
+        r = fn(fitted=fitted)
+        r["wall_s"] = time.perf_counter() - t0
+        out[name] = r
+        t0 = time.perf_counter()
     return out
 
 
@@ -343,14 +402,14 @@ def bench_fit_pool(steps=10):
 
 def main(argv):
     which = argv or ["fit", "penalty", "grouped", "tiny", "grouped_paper", "cloth", "paper_arch",
-                     "fit512", "fit_paper", "cloth_fitted"]
+                     "fit512", "fit_paper", "cloth_fitted", "voxel"]
     torch.cuda.set_device(0)
     for w in which:
         t0 = time.perf_counter()
         r = {"fit": bench_fit, "penalty": bench_penalty, "grouped": bench_grouped,
              "grouped_paper": bench_grouped_paper, "cloth": bench_cloth,
              "paper_arch": bench_paper_arch, "fit512": bench_fit512, "fit_paper": bench_fit_paper,
-             "cloth_fitted": bench_cloth_fitted, "tiny": bench_tiny}[w]()
+             "cloth_fitted": bench_cloth_fitted, "tiny": bench_tiny, "voxel": bench_voxel}[w]()
         r["wall_s"] = time.perf_counter() - t0
         print(json.dumps(r), flush=True)
 
