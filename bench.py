@@ -48,7 +48,7 @@ FLOP_PER_QUERY = 2 * MAC_PER_QUERY
 # only while that code is unchanged.
 TRAFFIC_CAPTURE = {
     "code_sha256": "2bc4adad8764c47ab635987a3d5a7343a1872f7a096418258943e63f7bbc2b47",
-    "bytes_per_launch": 3.64e9 + 4.58e9,
+    "bytes_per_launch": 4.018766e9 + 4.897754e9,
 }
 
 
