@@ -29,6 +29,19 @@
 // A training form of the same kernel (kSave) also writes every A operand out
 // for the weight-gradient products of the fitting loss (train.cu).
 //
+// Queries run in the CTA-pair form (kPair): the two CTAs of a cluster take
+// consecutive tiles, and the even CTA issues every product as M=256
+// tcgen05.mma over both (cta_group::2: each CTA's A rows, each CTA's 128
+// rows of the weight panel).  Each CTA then streams half a panel per
+// product step (a 4-stage ring of 16 KB in the same 64 KB), and the odd
+// CTA's epilogue hand-overs reach the even CTA's barriers through a relay
+// thread.  The training form keeps one CTA per product (2-stage ring of
+// 32 KB panels, each fetched half by each CTA and multicast).
+//
+// FP32 arithmetic of the epilogues (biases, the FP32 layers, the deltas and
+// the running sums) is issued as f32x2 pairs: scalar FP32 FMA-pipe streams
+// on the SM slow the products (softplus.cuh).
+//
 // BF16 operand rounding and its first-order correction.  Rounding the
 // 512-wide activations to BF16's 8-bit significand at each tensor-core layer
 // moves f by up to ~3.2e-3 on the body-scale network, while weight rounding
@@ -62,6 +75,10 @@ constexpr int kKAtom = 64;                 // K elements per 128-byte swizzle at
 // Weight-panel ring depth.  Two stages leave room for the small FP32 weights
 // below; the epilogue, not the weight stream, bounds the kernel.
 constexpr int kStages = 2;
+// CTA-pair form (cta_group::2): each product is one M=256 MMA chain over the
+// two CTAs' tiles, issued by the even CTA; each CTA holds its 128 rows of a
+// weight panel (16 KB), so the same 64 KB of ring make 4 stages.
+constexpr int kStagesPair = 4;
 // The biases of the first kMaxHidden layers, W_0, the skip layer's weights on
 // p and w_out stay in shared memory (30 KB, FP32); deeper layers read their
 // biases from global memory.
@@ -72,6 +89,8 @@ constexpr int kMaxHidden = 8;
 constexpr int kCluster = 2;
 constexpr int kSliceRows = 256 / kCluster;
 constexpr int kStageBytes = kN * kKAtom * 2;          // 32 KB weight panel
+constexpr int kStageBytesPair = kStageBytes / 2;      // 16 KB: this CTA's rows of a panel
+static_assert(kStagesPair * kStageBytesPair == kStages * kStageBytes, "same ring in both forms");
 constexpr int kABytes = kM * kW * 2;                  // 128 KB activation tile
 constexpr int kAtomBytes = kM * kKAtom * 2;           // 16 KB: one K atom of A
 constexpr int kLoadsPerLayer = (kW / kN) * (kW / kKAtom);   // 16
@@ -101,9 +120,9 @@ constexpr int kOffW0 = kOffBias + kMaxHidden * kW * 4;     // float [kW][3]
 constexpr int kOffWsk = kOffW0 + kW * 3 * 4;               // float [3][kW]: W_s[:, kW - 3 + j]
 constexpr int kOffWout = kOffWsk + 3 * kW * 4;             // float [kW]
 constexpr int kOffBar = kOffWout + kW * 4;
-// barriers: full[kStages], empty[kStages], a_lo, a_hi_a, a_hi_b, d0_full,
+// barriers: full[stages], empty[stages], a_lo, a_hi_a, a_hi_b, d0_full,
 // d1_full, lo_free_a, lo_free_b, mma_done, x_full, x_empty
-constexpr int kNumBars = 2 * kStages + 10;
+constexpr int kNumBars = 2 * kStagesPair + 10;
 
 // K atom taken at position pos (0..7) of column half nh.  Epilogue thread
 // group g (0, 1) writes atoms 4h + 2g (its first two chunks) and 4h + 2g + 1
@@ -248,10 +267,17 @@ __device__ __forceinline__ uint32_t comp_u(const uint4 &v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// Running sums of an epilogue thread: grad f (partial) and f (partial).
+// Running sums of an epilogue thread: grad f (partial) and f (partial), each
+// as two partial sums (even and odd columns, accumulated in f32x2).
 struct Acc {
-  float gx = 0.f, gy = 0.f, gz = 0.f, f = 0.f;
+  float2 gx = {0.f, 0.f}, gy = {0.f, 0.f}, gz = {0.f, 0.f}, f = {0.f, 0.f};
 };
+__device__ __forceinline__ float2 pair_of(const float4 &v, int u) {   // components u, u + 1
+  return u == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
+}
+__device__ __forceinline__ float2 raw_pair(const uint32_t (&raw)[32], int i) {
+  return make_float2(__uint_as_float(raw[i]), __uint_as_float(raw[i + 1]));
+}
 
 // The waits an epilogue of column half 0 passes before it overwrites A:
 // part 0 (its first two chunks, atoms 0 and 2) once half 1 has read atoms
@@ -343,10 +369,15 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
       }
       float z[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        z[u] = __uint_as_float(raw[4 * q + u]) + comp(bq, u);
+      for (int u = 0; u < 4; u += 2) {    // in f32x2
+        float2 zz = f2_add(raw_pair(raw, 4 * q + u), pair_of(bq, u));
         if (AT_SKIP)
-          z[u] = fmaf(kInvSqrt2, fmaf(comp(s0, u), e.px, fmaf(comp(s1, u), e.py, comp(s2, u) * e.pz)), z[u]);
+          zz = f2_fma(f2_splat(kInvSqrt2),
+                      f2_fma(pair_of(s0, u), f2_splat(e.px),
+                             f2_fma(pair_of(s1, u), f2_splat(e.py), f2_mul(pair_of(s2, u), f2_splat(e.pz)))),
+                      zz);
+        z[u] = zz.x;
+        z[u + 1] = zz.y;
       }
 #pragma unroll
       for (int v = 0; v < 2; ++v) {
@@ -381,29 +412,32 @@ __device__ __forceinline__ void fwd_chunk(const Epi &e, int l, int c0, const uin
       }
       float hv[4], sv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = 4 * q + u;
-        const int c = c0 + i;
-        float z = __uint_as_float(raw[i]) + comp(bq, u);
+      for (int u = 0; u < 4; u += 2) {    // columns u, u + 1 in f32x2
+        const int c = c0 + 4 * q + u;
+        float2 z = f2_add(raw_pair(raw, 4 * q + u), pair_of(bq, u));
         if (AT_SKIP)    // the skip input columns p / sqrt(2), in FP32
-          z = fmaf(kInvSqrt2, fmaf(comp(s0, u), e.px, fmaf(comp(s1, u), e.py, comp(s2, u) * e.pz)), z);
-        act_f32(z, e.neg_bl2e, e.inv_beta, hv[u], sv[u]);
+          z = f2_fma(f2_splat(kInvSqrt2),
+                     f2_fma(pair_of(s0, u), f2_splat(e.px),
+                            f2_fma(pair_of(s1, u), f2_splat(e.py), f2_mul(pair_of(s2, u), f2_splat(e.pz)))),
+                     z);
+        float2 h, sl;
+        act_f32x2(z, e.neg_bl2e, e.inv_beta, h, sl);
         if (LAST) {
-          const float wo = comp(wq, u);
-          acc.f = fmaf(wo, hv[u], acc.f);
-          if constexpr (kSave) {
-            if (u & 1) hx[2 * q + (u >> 1)] = Op<kF16>::pack(__uint_as_float(hx[2 * q + (u >> 1)]), hv[u]);
-            else hx[2 * q + (u >> 1)] = __float_as_uint(hv[u]);
-          }
-          hv[u] = sv[u] * wo;                        // delta_{L-1}
+          const float2 wo = pair_of(wq, u);
+          acc.f = f2_fma(wo, h, acc.f);
+          if constexpr (kSave) hx[2 * q + (u >> 1)] = Op<kF16>::pack(h.x, h.y);
+          h = f2_mul(sl, wo);                        // delta_{L-1}
           if (AT_SKIP) {                             // delta_s feeds the direct term
-            acc.gx = fmaf(hv[u], comp(s0, u) * kInvSqrt2, acc.gx);
-            acc.gy = fmaf(hv[u], comp(s1, u) * kInvSqrt2, acc.gy);
-            acc.gz = fmaf(hv[u], comp(s2, u) * kInvSqrt2, acc.gz);
+            acc.gx = f2_fma(h, f2_mul(pair_of(s0, u), f2_splat(kInvSqrt2)), acc.gx);
+            acc.gy = f2_fma(h, f2_mul(pair_of(s1, u), f2_splat(kInvSqrt2)), acc.gy);
+            acc.gz = f2_fma(h, f2_mul(pair_of(s2, u), f2_splat(kInvSqrt2)), acc.gz);
           }
         } else if (FEEDS_SKIP) {
-          hv[u] = (c < kNShort) ? hv[u] * kInvSqrt2 : 0.0f;
+          const float2 hs = f2_mul(h, f2_splat(kInvSqrt2));
+          h = make_float2(c < kNShort ? hs.x : 0.0f, c + 1 < kNShort ? hs.y : 0.0f);
         }
+        hv[u] = h.x; hv[u + 1] = h.y;
+        sv[u] = sl.x; sv[u + 1] = sl.y;
       }
       if constexpr (!kF16 && !LAST) {
         // BF16 form: the activation as FP16 into the slab, its 8-bit rounding as A
@@ -484,11 +518,21 @@ __device__ __forceinline__ void layer0(const Epi &e) {
                            w_b.z, w_b.w, w_c.x, w_c.y, w_c.z, w_c.w};
       float hv[4], sv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = c0 + 4 * q + u;
-        const float z = fmaf(w[3 * u], e.px, fmaf(w[3 * u + 1], e.py, fmaf(w[3 * u + 2], e.pz, comp(bq, u))));
-        act_f32(z, e.neg_bl2e, e.inv_beta, hv[u], sv[u]);
-        if (FEEDS_SKIP) hv[u] = (c < kNShort) ? hv[u] * kInvSqrt2 : 0.0f;
+      for (int v = 0; v < 2; ++v) {       // columns 2v, 2v + 1 of the four, in f32x2
+        const int u = 2 * v;
+        const float2 z = f2_fma(make_float2(w[3 * u], w[3 * u + 3]), f2_splat(e.px),
+                                f2_fma(make_float2(w[3 * u + 1], w[3 * u + 4]), f2_splat(e.py),
+                                       f2_fma(make_float2(w[3 * u + 2], w[3 * u + 5]), f2_splat(e.pz),
+                                              make_float2(comp(bq, u), comp(bq, u + 1)))));
+        float2 h2, s2;
+        act_f32x2(z, e.neg_bl2e, e.inv_beta, h2, s2);
+        if (FEEDS_SKIP) {
+          const float2 hs = f2_mul(h2, f2_splat(kInvSqrt2));
+          const int c = c0 + 4 * q + u;
+          h2 = make_float2(c < kNShort ? hs.x : 0.0f, c + 1 < kNShort ? hs.y : 0.0f);
+        }
+        hv[u] = h2.x; hv[u + 1] = h2.y;
+        sv[u] = s2.x; sv[u + 1] = s2.y;
       }
       if constexpr (kF16) {
         hw[2 * q] = Op<kF16>::pack(hv[0], hv[1]);
@@ -546,7 +590,7 @@ __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (
     }
     const float2 cs = __half22float2(__hadd2(c0h, c1h));
     const float c = cs.x + cs.y;
-    if (isfinite(c)) acc.f = fmaf(c, 1.0f / 1024.0f, acc.f);
+    if (isfinite(c)) acc.f.x = fmaf(c, 1.0f / 1024.0f, acc.f.x);
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -573,24 +617,28 @@ __device__ __forceinline__ void bwd_chunk(const Epi &e, int c0, const uint32_t (
     }
     float dv[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = 4 * q + u;
-      const int c = c0 + i;
-      float g = __uint_as_float(raw[i]);
-      if (AT_SKIP) g = (c < kNShort) ? g * kInvSqrt2 : 0.0f;
-      dv[u] = sv[u] * g;
+    for (int u = 0; u < 4; u += 2) {    // columns u, u + 1 in f32x2
+      const int c = c0 + 4 * q + u;
+      float2 g = raw_pair(raw, 4 * q + u);
+      if (AT_SKIP) {
+        const float2 gs = f2_mul(g, f2_splat(kInvSqrt2));
+        g = make_float2(c < kNShort ? gs.x : 0.0f, c + 1 < kNShort ? gs.y : 0.0f);
+      }
+      const float2 d = f2_mul(make_float2(sv[u], sv[u + 1]), g);
       if (MAKES_SKIP_DELTA) {                      // direct path to the input
-        acc.gx = fmaf(dv[u], comp(s0, u) * kInvSqrt2, acc.gx);
-        acc.gy = fmaf(dv[u], comp(s1, u) * kInvSqrt2, acc.gy);
-        acc.gz = fmaf(dv[u], comp(s2, u) * kInvSqrt2, acc.gz);
+        acc.gx = f2_fma(d, f2_mul(pair_of(s0, u), f2_splat(kInvSqrt2)), acc.gx);
+        acc.gy = f2_fma(d, f2_mul(pair_of(s1, u), f2_splat(kInvSqrt2)), acc.gy);
+        acc.gz = f2_fma(d, f2_mul(pair_of(s2, u), f2_splat(kInvSqrt2)), acc.gz);
       }
       if (TO_INPUT) {
         const float w[12] = {w_a.x, w_a.y, w_a.z, w_a.w, w_b.x, w_b.y,
                              w_b.z, w_b.w, w_c.x, w_c.y, w_c.z, w_c.w};
-        acc.gx = fmaf(dv[u], w[3 * u], acc.gx);
-        acc.gy = fmaf(dv[u], w[3 * u + 1], acc.gy);
-        acc.gz = fmaf(dv[u], w[3 * u + 2], acc.gz);
+        acc.gx = f2_fma(d, make_float2(w[3 * u], w[3 * u + 3]), acc.gx);
+        acc.gy = f2_fma(d, make_float2(w[3 * u + 1], w[3 * u + 4]), acc.gy);
+        acc.gz = f2_fma(d, make_float2(w[3 * u + 2], w[3 * u + 5]), acc.gz);
       }
+      dv[u] = d.x;
+      dv[u + 1] = d.y;
     }
     dw[2 * q] = Op<kF16>::pack(dv[0], dv[1]);
     dw[2 * q + 1] = Op<kF16>::pack(dv[2], dv[3]);
@@ -654,7 +702,10 @@ __device__ __forceinline__ void bwd_half(const Epi &e, int l, int h, Acc &acc, G
 
 // kSave: the training form, which also writes every layer's A operand out
 // (QueryParams::save_h / save_d) for the weight-gradient products.
-template <bool kF16, bool kSave = false>
+// kPair: the CTA-pair form (M=256 products over the cluster's two tiles,
+// issued by the even CTA; the odd CTA's hand-overs are forwarded to the even
+// CTA's barriers by a relay thread).
+template <bool kF16, bool kSave = false, bool kPair = false>
 __global__ void __launch_bounds__(kThreads, 1)
     query_tc16_kernel(const QueryParams prm, const __grid_constant__ CUtensorMap tmap_fwd,
                       const __grid_constant__ CUtensorMap tmap_bwd) {
@@ -668,11 +719,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t *A = smem + kOffA;
   const uint32_t sA = smem_u32(A), sB = smem_u32(smem + kOffB);
   const uint32_t bar0 = smem_u32(smem + kOffBar);
+  constexpr int S = kPair ? kStagesPair : kStages;          // ring stages
+  constexpr int SB = kPair ? kStageBytesPair : kStageBytes;  // bytes of a stage in this CTA
+  const uint32_t crank = cluster_rank();
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
   // epilogue -> MMA: A atoms 0..3 written (and TMEM half 0 read); atoms 4, 6;
   // atoms 5, 7 (and TMEM half 1 read)
-  const uint32_t a_lo = bar0 + 8u * (2 * kStages);
+  const uint32_t a_lo = bar0 + 8u * (2 * S);
   const uint32_t a_hi_a = a_lo + 8u;
   const uint32_t a_hi_b = a_hi_a + 8u;
   // MMA -> epilogue: column half 0 / 1 of the product in TMEM; half 1 has
@@ -694,13 +748,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   const long long budget = prm.wait_budget;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), kCluster);   // freed when every CTA of the cluster consumed it
+      // freed when every CTA of the cluster consumed it (pair: the even CTA's
+      // products read both CTAs' stages; its commit reaches both)
+      mbar_init(empty_bar(s), kPair ? 1 : kCluster);
     }
-    mbar_init(a_lo, kEpiWarps);
-    mbar_init(a_hi_a, kEpiWarps);
-    mbar_init(a_hi_b, kEpiWarps);
+    // pair: the even CTA's gates also count the odd CTA's relayed arrival
+    const uint32_t gate_count = kEpiWarps + ((kPair && crank == 0) ? 1 : 0);
+    mbar_init(a_lo, gate_count);
+    mbar_init(a_hi_a, gate_count);
+    mbar_init(a_hi_b, gate_count);
     mbar_init(d0_full, 1);
     mbar_init(d1_full, 1);
     mbar_init(lo_free_a, 1);
@@ -733,17 +791,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = threadIdx.x; i < kW / 4; i += kThreads) dst[i] = __ldg(wosrc + i);
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                     smem_u32(smem + kOffTmemSlot)),
-                 "r"(kW));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    if constexpr (kPair) {   // one warp of each CTA of the pair allocates collectively
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                       smem_u32(smem + kOffTmemSlot)),
+                   "r"(kW));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;\n");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                       smem_u32(smem + kOffTmemSlot)),
+                   "r"(kW));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
   }
   tc_fence_before();
   __syncthreads();
   cluster_sync();      // every CTA's barriers exist before any multicast targets them
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t crank = cluster_rank();
   const uint16_t cmask = (uint16_t)((1u << kCluster) - 1u);
   // every CTA walks the same number of tiles (the cluster's CTAs consume the
   // same weight panels in lockstep); tiles past the end are all-masked
@@ -763,7 +827,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     cluster_sync();
     if (tmem_owner) {
       tc_fence_after();
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kW));
+      if constexpr (kPair)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kW));
+      else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kW));
     }
   };
 
@@ -791,28 +858,49 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const int nh = ld / (kW / kKAtom), kb = k_atom(nh, ld % (kW / kKAtom));
             if (load_idx != prm.drop_load) {
-              mbar_expect_tx(full_bar(stage), kStageBytes);   // all slices land here
-              tma_load_2d_mc(sB + stage * kStageBytes + crank * (kSliceRows * kKAtom * 2), map,
-                             kb * kKAtom, rowbase + nh * kN + (int)crank * kSliceRows,
-                             full_bar(stage), cmask);
+              if constexpr (kPair) {
+                // this CTA's 128 rows of the panel; both halves count on the
+                // even CTA's barrier, which expects them both
+                if (crank == 0) mbar_expect_tx(full_bar(stage), 2 * SB);
+                tma_load_2d_pair(sB + stage * SB, map, kb * kKAtom,
+                                 rowbase + nh * kN + (int)crank * kSliceRows,
+                                 map_to_rank(full_bar(stage), 0));
+              } else {
+                mbar_expect_tx(full_bar(stage), kStageBytes);   // all slices land here
+                tma_load_2d_mc(sB + stage * kStageBytes + crank * (kSliceRows * kKAtom * 2), map,
+                               kb * kKAtom, rowbase + nh * kN + (int)crank * kSliceRows,
+                               full_bar(stage), cmask);
+              }
               issued_mask |= 1u << stage;
               issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
             }
-            if (++stage == kStages) stage = 0, phase ^= 1u;
+            if (++stage == S) stage = 0, phase ^= 1u;
           }
         }
       }
-      // drain: every issued load must land before the CTA may exit
-      for (int s = 0; s < kStages; ++s) {
-        if (issued_mask & (1u << s)) {
-          volatile int no_abort = 0;
-          if (!mbar_wait<true>(full_bar(s), (issued_parity >> s) & 1u, budget, &no_abort)) fail();
+      // drain: every issued load must land before the CTA may exit (pair: the
+      // even CTA's barriers count both CTAs' halves)
+      if (!kPair || crank == 0) {
+        for (int s = 0; s < S; ++s) {
+          if (issued_mask & (1u << s)) {
+            volatile int no_abort = 0;
+            if (!mbar_wait<true>(full_bar(s), (issued_parity >> s) & 1u, budget, &no_abort)) fail();
+          }
         }
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
+    if (lane == 0 && (!kPair || crank == 0)) {
+      // ---------------- MMA issuer (pair form: the even CTA) ----------------
+      // descriptors of A atom 0 and ring stage 0; atoms, stages and K steps
+      // are constant offsets (addresses below 256 KB: no carry out of the
+      // 14-bit address field)
+      const uint64_t adesc0 = sw128_desc(sA), bdesc0 = sw128_desc(sB);
+      constexpr uint32_t idesc = kPair ? idesc_f16(kF16, 2 * kM, kN) : Op<kF16>::idesc;
+      auto commit_both = [&](uint32_t bar) {     // pair form: reaches both CTAs
+        if constexpr (kPair) mma_commit_pair_mc(bar, cmask);
+        else mma_commit(bar);
+      };
       int stage = 0;
       uint32_t phase = 0, a_phase = 0;
       bool ok = true;
@@ -824,7 +912,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             // starts, atoms 4, 6 and then 5, 7 (and TMEM half 1 read) later
             if (nh == 0 && (pos == 0 || pos == 4 || pos == 6)) {
               const uint32_t bar = pos == 0 ? a_lo : (pos == 4 ? a_hi_a : a_hi_b);
-              if (!mbar_wait<true>(bar, a_phase, budget, abort_flag)) {
+              const bool got = kPair ? mbar_wait_cluster(bar, a_phase, budget, abort_flag)
+                                     : mbar_wait<true>(bar, a_phase, budget, abort_flag);
+              if (!got) {
                 fail();
                 ok = false;
                 break;
@@ -838,28 +928,53 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(nh * kN);
-            const uint32_t a_atom = sA + kb * kAtomBytes;
-            const uint32_t b_stage = sB + stage * kStageBytes;
+            const uint64_t ad = adesc0 + (uint64_t)(kb * (kAtomBytes >> 4));
+            const uint64_t bd = bdesc0 + (uint64_t)(stage * (SB >> 4));
 #pragma unroll
             for (int ks = 0; ks < kKAtom / 16; ++ks) {
-              mma_f16(d, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32),
-                     Op<kF16>::idesc, (pos | ks) != 0 ? 1u : 0u);
+              const uint32_t acc = (pos | ks) != 0 ? 1u : 0u;
+              if constexpr (kPair) mma_f16_pair(d, ad + 2 * ks, bd + 2 * ks, idesc, acc);
+              else mma_f16(d, ad + 2 * ks, bd + 2 * ks, idesc, acc);
             }
-            mma_commit_mc(empty_bar(stage), cmask);
-            if (++stage == kStages) stage = 0, phase ^= 1u;
-            if (nh == 0 && pos == 7) mma_commit(d0_full);
-            else if (nh == 1 && pos == 1) mma_commit(lo_free_a);
-            else if (nh == 1 && pos == 3) mma_commit(lo_free_b);
+            if constexpr (kPair) mma_commit_pair_mc(empty_bar(stage), cmask);
+            else mma_commit_mc(empty_bar(stage), cmask);
+            if (++stage == S) stage = 0, phase ^= 1u;
+            if (nh == 0 && pos == 7) commit_both(d0_full);
+            else if (nh == 1 && pos == 1) commit_both(lo_free_a);
+            else if (nh == 1 && pos == 3) commit_both(lo_free_b);
           }
           if (!ok) break;
           a_phase ^= 1u;
-          mma_commit(d1_full);
+          commit_both(d1_full);
         }
       }
       // drain: no product may still be writing TMEM when it is freed
-      mma_commit(mma_done);
+      if constexpr (kPair) mma_commit_pair(mma_done);
+      else mma_commit(mma_done);
       volatile int no_abort = 0;
       if (!mbar_wait<true>(mma_done, 0, budget, &no_abort)) fail();
+    } else if (kPair && lane == 0) {
+      // ---------------- relay (pair form: the odd CTA) ----------------
+      // forwards each completed phase of this CTA's epilogue gates to the
+      // even CTA's gates, in the order the products consume them
+      const uint32_t remote[3] = {map_to_rank(a_lo, 0), map_to_rank(a_hi_a, 0),
+                                  map_to_rank(a_hi_b, 0)};
+      const uint32_t local[3] = {a_lo, a_hi_a, a_hi_b};
+      uint32_t a_phase = 0;
+      bool ok = true;
+      for (int64_t it = 0; ok && it < iters; ++it) {
+        for (int li = 0; ok && li < G; ++li) {
+          for (int g = 0; g < 3; ++g) {
+            if (!mbar_wait<true>(local[g], a_phase, budget, abort_flag)) {
+              fail();
+              ok = false;
+              break;
+            }
+            mbar_arrive_remote(remote[g]);
+          }
+          a_phase ^= 1u;
+        }
+      }
     }
   }
   finish(warp == 1);
@@ -902,7 +1017,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       return true;
     };
     for (int64_t it = 0; ok && it < iters; ++it) {
-      const int64_t tile = blockIdx.x + it * gridDim.x;
+      // pair form: the cluster's two CTAs take consecutive tiles (rows 0..127
+      // and 128..255 of each M=256 product)
+      const int64_t tile = kPair ? ((int64_t)(blockIdx.x >> 1) + it * (gridDim.x >> 1)) * 2 + crank
+                                 : blockIdx.x + it * gridDim.x;
       const int64_t idx = tile * kM + r;
       e.row = idx;
       float4 pw = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -977,7 +1095,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         d_phase ^= 1u;
       }
       if (!ok) break;
-      float gx = acc.gx, gy = acc.gy, gz = acc.gz, fpart = acc.f;
+      float gx = acc.gx.x + acc.gx.y, gy = acc.gy.x + acc.gy.y, gz = acc.gz.x + acc.gz.y;
+      float fpart = acc.f.x + acc.f.y;
 
       // ---- a7-a9: combine the two column halves, normalise, test, project ----
       if (ch == 1) {
@@ -1060,7 +1179,7 @@ static int resident_cluster_ctas(int num_sms) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev] < num_sms ? cached[dev] : num_sms;
-  cudaFuncSetAttribute(query_tc16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaFuncSetAttribute(query_tc16_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kCluster * 256, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
@@ -1073,7 +1192,7 @@ static int resident_cluster_ctas(int num_sms) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, query_tc16_kernel<false>, &cfg) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveClusters(&clusters, query_tc16_kernel<false, false, true>, &cfg) != cudaSuccess ||
       clusters < 1) {
     cudaGetLastError();
     clusters = num_sms / kCluster;
@@ -1103,15 +1222,15 @@ size_t query_tc16_scratch_bytes(int width, int n_hidden, int grid, bool fp16) {
   return (size_t)grid * (size_t)(n_hidden - 1) * kW * kM * 2;
 }
 
-template <bool kF16, bool kSave>
+template <bool kF16, bool kSave, bool kPair>
 cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cudaStream_t s) {
+  auto kern = query_tc16_kernel<kF16, kSave, kPair>;
   // the register split inside the kernel is only valid for this count
   cudaFuncAttributes fa{};
-  cudaError_t e = cudaFuncGetAttributes(&fa, query_tc16_kernel<kF16, kSave>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
   if (fa.numRegs != kLaunchRegs) return cudaErrorInvalidConfiguration;
-  e = cudaFuncSetAttribute(query_tc16_kernel<kF16, kSave>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   const int grid = query_tc16_grid(p.width, p.n, num_sms);
   cudaLaunchConfig_t cfg = {};
@@ -1126,16 +1245,20 @@ cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cu
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, query_tc16_kernel<kF16, kSave>, p, net.tmap_fwd, net.tmap_bwd);
+  e = cudaLaunchKernelEx(&cfg, kern, p, net.tmap_fwd, net.tmap_bwd);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
+// Queries run in the CTA-pair form; the training form (which also writes
+// every A operand out) keeps one CTA per product.
 cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bool fp16,
                                   int num_sms, cudaStream_t s) {
   if (p.save_h)
-    return fp16 ? launch_t<true, true>(p, net, num_sms, s) : launch_t<false, true>(p, net, num_sms, s);
-  return fp16 ? launch_t<true, false>(p, net, num_sms, s) : launch_t<false, false>(p, net, num_sms, s);
+    return fp16 ? launch_t<true, true, false>(p, net, num_sms, s)
+                : launch_t<false, true, false>(p, net, num_sms, s);
+  return fp16 ? launch_t<true, false, true>(p, net, num_sms, s)
+              : launch_t<false, false, true>(p, net, num_sms, s);
 }
 
 }  // namespace nsdf

@@ -38,4 +38,58 @@ __device__ __forceinline__ void act_f32(float z, float neg_bl2e, float inv_beta,
   s = (z >= 0.0f) ? r : u * r;
 }
 
+// Two FP32 lanes per instruction (f32x2).  Each lane is the IEEE single
+// result of the scalar operation with round-to-nearest, so these replace
+// pairs of scalar FADD/FMUL/FFMA with identical values.  They also matter
+// for speed beside the tensor cores: a stream of scalar FP32 FMA-pipe
+// instructions on an SM slows the tcgen05 products issued there (measured
+// with back-to-back M=128 N=256 products: 128 cycles each alone, 342 with
+// eight warps of scalar FFMA, 128 with the same work in f32x2, HFMA2 or
+// integer instructions).
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n"
+      " add.rn.f32x2 d, a, b;\n mov.b64 {%0, %1}, d;\n}\n"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n"
+      " mul.rn.f32x2 d, a, b;\n mov.b64 {%0, %1}, d;\n}\n"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+// a * b + c per lane, one rounding
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 a, b, c, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n"
+      " mov.b64 c, {%6, %7};\n fma.rn.f32x2 d, a, b, c;\n mov.b64 {%0, %1}, d;\n}\n"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_splat(float v) { return make_float2(v, v); }
+
+// act_f32 for two elements at once (the same operations per lane, so the
+// same values): softplus_beta(z) in h and its slope in s.
+__device__ __forceinline__ void act_f32x2(float2 z, float neg_bl2e, float inv_beta, float2 &h,
+                                          float2 &s) {
+  const float2 az = make_float2(__uint_as_float(__float_as_uint(z.x) & 0x7fffffffu),
+                                __uint_as_float(__float_as_uint(z.y) & 0x7fffffffu));
+  const float2 t = f2_mul(az, f2_splat(neg_bl2e));
+  const float2 u = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+  float2 p = f2_splat(-2.344365580e-02f);
+  p = f2_fma(p, u, f2_splat(1.001397327e-01f));
+  p = f2_fma(p, u, f2_splat(-2.090795360e-01f));
+  p = f2_fma(p, u, f2_splat(3.248495807e-01f));
+  p = f2_fma(p, u, f2_splat(-4.993146523e-01f));
+  p = f2_fma(p, u, f2_splat(9.999905920e-01f));
+  h = f2_fma(f2_mul(u, p), f2_splat(inv_beta), make_float2(fmaxf(z.x, 0.0f), fmaxf(z.y, 0.0f)));
+  const float2 d = f2_add(f2_splat(1.0f), u);
+  const float2 r = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+  const float2 ur = f2_mul(u, r);
+  s = make_float2(z.x >= 0.0f ? r.x : ur.x, z.y >= 0.0f ? r.y : ur.y);
+}
+
 }  // namespace nsdf
