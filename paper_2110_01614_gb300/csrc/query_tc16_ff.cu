@@ -62,6 +62,7 @@
 
 #include "nsdf_internal.h"
 #include "tc_ptx.cuh"
+#include "f32x2.cuh"
 #include "ff_phase.cuh"
 
 namespace nsdf {
@@ -165,12 +166,17 @@ __device__ __forceinline__ uint32_t fwd_chunk(int l, int c0, const uint32_t (&ra
     const float4 b = lds4(kOffBias, (l * kW + c0) / 4 + q);
     float4 wo = make_float4(0.f, 0.f, 0.f, 0.f);
     if (LAST) wo = lds4(kOffWout, c0 / 4 + q);
-    const float bv[4] = {b.x, b.y, b.z, b.w};
     const float wv[4] = {wo.x, wo.y, wo.z, wo.w};
+    // the bias in f32x2 (scalar FP32 streams slow the products on this SM)
+    const float2 z01 = f2_add(make_float2(__uint_as_float(raw[4 * q]), __uint_as_float(raw[4 * q + 1])),
+                              make_float2(b.x, b.y));
+    const float2 z23 = f2_add(make_float2(__uint_as_float(raw[4 * q + 2]), __uint_as_float(raw[4 * q + 3])),
+                              make_float2(b.z, b.w));
+    const float zv[4] = {z01.x, z01.y, z23.x, z23.y};
     float v[4], hv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const float z = __uint_as_float(raw[4 * q + u]) + bv[u];
+      const float z = zv[u];
       const bool pos = z > 0.0f;
       bits |= (pos ? 1u : 0u) << (4 * q + u);
       const float h = pos ? z : 0.0f;
