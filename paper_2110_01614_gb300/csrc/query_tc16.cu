@@ -1250,13 +1250,12 @@ cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cu
   return cudaGetLastError();
 }
 
-// Queries run in the CTA-pair form; the training form (which also writes
-// every A operand out) keeps one CTA per product.
+// Queries and the training form both run as CTA pairs.
 cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bool fp16,
                                   int num_sms, cudaStream_t s) {
   if (p.save_h)
-    return fp16 ? launch_t<true, true, false>(p, net, num_sms, s)
-                : launch_t<false, true, false>(p, net, num_sms, s);
+    return fp16 ? launch_t<true, true, true>(p, net, num_sms, s)
+                : launch_t<false, true, true>(p, net, num_sms, s);
   return fp16 ? launch_t<true, false, true>(p, net, num_sms, s)
               : launch_t<false, false, true>(p, net, num_sms, s);
 }
