@@ -45,6 +45,15 @@ nsdf_status nsdf_debug_noalloc_limit(size_t bytes);
  */
 nsdf_status nsdf_debug_fp32_fma_peak(double *tflops, nsdf_stream stream);
 
+/*
+ * Selects how later launches of the width-512 tensor-core kernel issue their
+ * products (process-wide): 1 = one CTA per 128-point tile (M=128 products, a
+ * 2-stage ring of 32 KB weight panels), 0 = the default CTA pairs (M=256
+ * products over a 2-CTA cluster's two tiles).  Both compute the same values;
+ * this lets a test and a timing compare them.  Host-side only.
+ */
+nsdf_status nsdf_debug_tc16_one_cta(int enable);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ __all__ = [
     "nsdf_query_grouped_T", "nsdf_l1_grad",
     "nsdf_autotune_grouped", "nsdf_set_grouped_config",
     "nsdf_mesh_sdf", "nsdf_cloth_step", "nsdf_sync_status", "nsdf_debug_inject",
-    "nsdf_debug_noalloc_limit", "nsdf_debug_fp32_fma_peak", "nsdf_voxel_build",
+    "nsdf_debug_noalloc_limit", "nsdf_debug_fp32_fma_peak", "nsdf_debug_tc16_one_cta", "nsdf_voxel_build",
     "nsdf_voxel_collide",
     "nsdf_status_string", "NeuralSDF", "library",
 ]
@@ -204,6 +204,11 @@ def nsdf_debug_inject(ctx, drop_load=-1, wait_budget_cycles=4_000_000_000):
     """Test-only: drop one weight-panel load and/or shorten the kernel's bounded waits."""
     _check(library().nsdf_debug_inject(ctx, int(drop_load), int(wait_budget_cycles)),
            "nsdf_debug_inject")
+
+
+def nsdf_debug_tc16_one_cta(enable):
+    """Width-512 tensor-core launches after this use one CTA per tile (True) or CTA pairs (False, the default)."""
+    _check(library().nsdf_debug_tc16_one_cta(1 if enable else 0), "nsdf_debug_tc16_one_cta")
 
 
 def nsdf_debug_noalloc_limit(nbytes):

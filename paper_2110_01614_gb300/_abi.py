@@ -71,6 +71,7 @@ SIGNATURES = {
     "nsdf_debug_inject": (_ST, [_P, ctypes.c_int, ctypes.c_longlong]),
     "nsdf_debug_noalloc_limit": (_ST, [ctypes.c_size_t]),
     "nsdf_debug_fp32_fma_peak": (_ST, [ctypes.POINTER(ctypes.c_double), _P]),
+    "nsdf_debug_tc16_one_cta": (_ST, [ctypes.c_int]),
 }
 
 _lib = None

@@ -59,6 +59,9 @@
 
 #include <cudaTypedefs.h>
 
+#include <atomic>
+
+#include "nsdf_debug.h"
 #include "nsdf_internal.h"
 #include "softplus.cuh"
 #include "tc_ptx.cuh"
@@ -1250,9 +1253,19 @@ cudaError_t launch_t(const QueryParams &p, const NetDevice &net, int num_sms, cu
   return cudaGetLastError();
 }
 
-// Queries and the training form both run as CTA pairs.
+// Queries and the training form both run as CTA pairs unless the one-CTA
+// form is selected (nsdf_debug_tc16_one_cta).
+std::atomic<int> g_one_cta{0};
+
 cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bool fp16,
                                   int num_sms, cudaStream_t s) {
+  if (g_one_cta.load(std::memory_order_relaxed)) {
+    if (p.save_h)
+      return fp16 ? launch_t<true, true, false>(p, net, num_sms, s)
+                  : launch_t<false, true, false>(p, net, num_sms, s);
+    return fp16 ? launch_t<true, false, false>(p, net, num_sms, s)
+                : launch_t<false, false, false>(p, net, num_sms, s);
+  }
   if (p.save_h)
     return fp16 ? launch_t<true, true, true>(p, net, num_sms, s)
                 : launch_t<false, true, true>(p, net, num_sms, s);
@@ -1261,3 +1274,8 @@ cudaError_t launch_query_tc16_net(const QueryParams &p, const NetDevice &net, bo
 }
 
 }  // namespace nsdf
+
+extern "C" nsdf_status nsdf_debug_tc16_one_cta(int enable) {
+  nsdf::g_one_cta.store(enable ? 1 : 0, std::memory_order_relaxed);
+  return NSDF_OK;
+}

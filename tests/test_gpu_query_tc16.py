@@ -174,3 +174,22 @@ def test_full_size_sampled_parity(nsdf, prec, blob):
     nrm = np.linalg.norm(out_ns[:, :3], axis=1)
     assert np.all(np.abs(nrm - 1.0) < 1e-5)
     np.testing.assert_array_equal(out_hit, out_ns[:, 3] < EPS)
+
+
+@pytest.mark.parametrize("n", [129, 40000])
+def test_one_cta_form_matches_pairs_and_oracle(nsdf, prec, blob, n):
+    """The one-CTA form (M=128 products) against the default CTA pairs (M=256
+    products over two tiles): the same per-row products in the same K order,
+    so every output is bit-equal; and against the oracle at the stated
+    tolerances.  n=129 leaves the second CTA of a pair on a masked tile."""
+    pts = synth.body_scale_points(n, 11)
+    pair = collide_gpu(nsdf, prec, blob, pts)
+    nsdf.nsdf_debug_tc16_one_cta(True)
+    try:
+        one = collide_gpu(nsdf, prec, blob, pts)
+    finally:
+        nsdf.nsdf_debug_tc16_one_cta(False)
+    for a, b in zip(pair, one):
+        np.testing.assert_array_equal(a, b)
+    f, N, hit, x = mlp.collide(blob, BODY, pts, EPS)
+    check(prec, f, N, hit, x, *one, pts)
