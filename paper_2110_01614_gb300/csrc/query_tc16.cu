@@ -75,12 +75,14 @@ constexpr int kW = 512;                    // network width handled here
 constexpr int kM = 128;                    // points per tile (MMA M, TMEM lanes)
 constexpr int kN = 256;                    // MMA N (one half of a layer)
 constexpr int kKAtom = 64;                 // K elements per 128-byte swizzle atom
-// Weight-panel ring depth.  Two stages leave room for the small FP32 weights
-// below; the epilogue, not the weight stream, bounds the kernel.
+// Weight-panel ring depth of the one-CTA form: two 32 KB stages leave room
+// for the small FP32 weights below.
 constexpr int kStages = 2;
 // CTA-pair form (cta_group::2): each product is one M=256 MMA chain over the
 // two CTAs' tiles, issued by the even CTA; each CTA holds its 128 rows of a
-// weight panel (16 KB), so the same 64 KB of ring make 4 stages.
+// weight panel (16 KB), so the same 64 KB of ring make 4 stages.  (A fifth
+// stage, made room for by reading W_0, the skip weights and w_out through L1,
+// measured 0.3% faster than 4 with the same L1 reads, which cost 2%.)
 constexpr int kStagesPair = 4;
 // The biases of the first kMaxHidden layers, W_0, the skip layer's weights on
 // p and w_out stay in shared memory (30 KB, FP32); deeper layers read their
