@@ -473,6 +473,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f16(kF16, kM, kN);
+      // descriptors of A atom 0 and ring stage 0; atoms, stages and K steps
+      // are constant offsets (addresses below 256 KB: no carry out of the
+      // 14-bit address field)
+      const uint64_t adesc0 = sw128_desc(sA), bdesc0 = sw128_desc(sB);
       int stage = 0;
       uint32_t phase = 0, a_phase = 0;
       bool ok = true;
@@ -487,12 +491,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t a_atom = sA + k * kAtomBytes;
-            const uint32_t b_stage = sB + stage * kStageBytes;
+            const uint64_t ad = adesc0 + (uint64_t)(k * (kAtomBytes >> 4));
+            const uint64_t bd = bdesc0 + (uint64_t)(stage * (kStageBytes >> 4));
 #pragma unroll
             for (int ks = 0; ks < kKAtom / 16; ++ks)
-              mma_f16(d, sw128_desc(a_atom + ks * 32), sw128_desc(b_stage + ks * 32), idesc,
-                      (k | ks) != 0 ? 1u : 0u);
+              mma_f16(d, ad + 2 * ks, bd + 2 * ks, idesc, (k | ks) != 0 ? 1u : 0u);
             mma_commit_mc(empty_bar(stage), cmask);
             if (++stage == kStages) stage = 0, phase ^= 1u;
           }
