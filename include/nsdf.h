@@ -191,7 +191,9 @@ nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int64_t n,
  * per point (w ignored) and nullable (= 0).  g_weights (nullable) receives
  * dL/dtheta in blob layout (overwritten, FP32, nsdf_num_params floats);
  * g_pts (nullable) receives dL/dp_i as float4 (w = 0).  Layer activations
- * are recomputed, not stored.  FP32 arithmetic for either precision.
+ * are recomputed, not stored.  FP32 arithmetic for either precision.  Every
+ * array is DEVICE memory (host memory: NSDF_ERR_INVALID_ARG, nothing is
+ * launched).
  */
 nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n,
                           const float *g_sdf, const float *g_grad,
@@ -212,8 +214,8 @@ nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n,
  * the first call and when n grows.  Fourier-feature ReLU contexts (Sec. 4.3)
  * take the same route through their own tensor-core kernel; their
  * frequencies B are not trained (random Fourier features) and receive 0.
- * FP32 contexts: NSDF_ERR_UNSUPPORTED (use nsdf_backward); n = 0:
- * NSDF_ERR_INVALID_ARG.
+ * FP32 contexts: NSDF_ERR_UNSUPPORTED (use nsdf_backward); n = 0 or a host
+ * array: NSDF_ERR_INVALID_ARG.
  */
 nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n,
                          const float *targets, float *g_weights, float *loss,
@@ -227,7 +229,9 @@ nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n,
  * CUDA graph that captured this call replays correctly with new counts.
  * max_total bounds offsets[k] + counts[k] (a violating entry is skipped and
  * reported by nsdf_sync_status as NSDF_ERR_INVALID_ARG) and sizes the launch.
- * out_n_sdf nullable; points outside every range are left untouched.
+ * out_n_sdf nullable; points outside every range are left untouched.  pts,
+ * out_pts and out_n_sdf are DEVICE memory too (a host array, or host
+ * offsets / counts: NSDF_ERR_INVALID_ARG, nothing is launched).
  * Arithmetic: FP32 contexts run the FP32 fused kernel; 16-bit width-64
  * softplus and Fourier-feature ReLU contexts run the tensor-core kernel of
  * their shape and precision with the same results per point as
@@ -319,7 +323,8 @@ nsdf_status nsdf_voxel_collide(const float *grid, int n, const float *lo,
  * (the targets of Sec. 3.1): out_sdf[i] = +-min_t dist(p_i, triangle t),
  * negative where the generalized winding number exceeds 1/2 (interior
  * negative, Sec. 3.2).  verts: float [n_verts*3]; faces: int32 [n_faces*3],
- * counter-clockwise seen from outside; pts float4; all device pointers.
+ * counter-clockwise seen from outside; pts float4; all device pointers (a
+ * host array: NSDF_ERR_INVALID_ARG, nothing is launched).
  * The winding number is accumulated in FP32 and recomputed in FP64 for
  * points with |w - 1/2| < 0.25 or distance < 1e-3.
  */
@@ -334,7 +339,8 @@ nsdf_status nsdf_mesh_sdf(const float *verts, int64_t n_verts,
  * shear springs with rest lengths from the grid spacings hx (along rows) and
  * hz (between rows), unit mass, Hooke constant k_over_m, gravity (0, -g, 0):
  *   x_new = 2 x - x_prev + dt^2 a(x).
- * Writes x_new into x_prev's buffer (the caller swaps the two).  The
+ * Writes x_new into x_prev's buffer (the caller swaps the two).  x and
+ * x_prev_inout are DEVICE memory (host memory: NSDF_ERR_INVALID_ARG).  The
  * collision solve is a separate nsdf_collide call on the result.
  */
 nsdf_status nsdf_cloth_step(const float *x, float *x_prev_inout, int nx,

@@ -44,17 +44,8 @@ int layer_in(const nsdf_arch &a, int l) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// 0: device (or managed), 1: host (pinned or pageable), -1: error
-int pointer_kind(const void *p) {
-  cudaPointerAttributes attr;
-  cudaError_t e = cudaPointerGetAttributes(&attr, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return 1;
-  }
-  if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) return 0;
-  return 1;
-}
+// 0: device (or managed), 1: host (pinned or pageable, or unknown to CUDA)
+int pointer_kind(const void *p) { return device_memory(p) ? 0 : 1; }
 
 bool invert4x4(const double *m, double *inv) {
   double a[4][8];
@@ -397,6 +388,15 @@ nsdf_status collide_host(nsdf_ctx *ctx, QueryParams base, const float *pts, int6
 
 namespace nsdf {
 
+bool device_memory(const void *p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
 nsdf_status ctx_query_setup(nsdf_ctx *ctx, QueryParams *p, int *num_sms, int *width,
                             int *n_hidden, bool *tc16, bool *fp16, const NetDevice **net) {
   if (!ctx->nets[0].loaded) return NSDF_ERR_NOT_LOADED;
@@ -682,12 +682,16 @@ nsdf_status nsdf_backward(nsdf_ctx *ctx, const float *pts, int64_t n, const floa
   const int64_t n_params = (int64_t)nsdf_num_params(&a);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (n == 0) {
+    if (g_weights && !device_memory(g_weights)) return NSDF_ERR_INVALID_ARG;
     if (g_weights) return map_err(cudaMemsetAsync(g_weights, 0, sizeof(float) * n_params, s));
     return NSDF_OK;
   }
   if (!pts || !g_sdf || (!g_weights && !g_pts)) return NSDF_ERR_INVALID_ARG;
   if (!aligned16(pts) || (g_grad && !aligned16(g_grad)) || (g_pts && !aligned16(g_pts)))
     return NSDF_ERR_MISALIGNED;
+  if (!device_memory(pts) || !device_memory(g_sdf) || (g_grad && !device_memory(g_grad)) ||
+      (g_weights && !device_memory(g_weights)) || (g_pts && !device_memory(g_pts)))
+    return NSDF_ERR_INVALID_ARG;
   if (!g_grad && !g_weights) {
     // first order only: dL/dp = g_sdf * grad f, through the FP32 query kernel
     if (!query_fp32_supported(a.width)) return NSDF_ERR_UNSUPPORTED;
@@ -758,6 +762,10 @@ nsdf_status grouped_check(nsdf_ctx *ctx, const GroupedArgs &g) {
     return NSDF_ERR_MISALIGNED;
   if ((reinterpret_cast<uintptr_t>(g.offsets) & 7u) || (reinterpret_cast<uintptr_t>(g.counts) & 7u))
     return NSDF_ERR_MISALIGNED;
+  if (!device_memory(g.pts) || !device_memory(g.offsets) || !device_memory(g.counts) ||
+      !device_memory(g.out_pts) || (g.out_n_sdf && !device_memory(g.out_n_sdf)) ||
+      (g.T && !device_memory(g.T)))
+    return NSDF_ERR_INVALID_ARG;
   for (int k = 0; k < ctx->n_nets; ++k)
     if (!ctx->nets[k].loaded) return NSDF_ERR_NOT_LOADED;
   if (!query_fp32_supported(ctx->arch.width)) return NSDF_ERR_UNSUPPORTED;

@@ -61,6 +61,7 @@ extern "C" nsdf_status nsdf_cloth_step(const float *x, float *x_prev_inout, int 
   if (!x || !x_prev_inout || x == x_prev_inout || ny > 65535) return NSDF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(x) & 15u) || (reinterpret_cast<uintptr_t>(x_prev_inout) & 15u))
     return NSDF_ERR_MISALIGNED;
+  if (!nsdf::device_memory(x) || !nsdf::device_memory(x_prev_inout)) return NSDF_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   dim3 grid((nx + 255) / 256, ny);
   nsdf::cloth_step_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float4 *>(x),

@@ -233,6 +233,9 @@ extern "C" nsdf_status nsdf_mesh_sdf(const float *verts, int64_t n_verts, const 
   if (n == 0) return NSDF_OK;
   if (!verts || !faces || !pts || !out_sdf || n_faces == 0 || n_verts < 3) return NSDF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(pts) & 15u) != 0) return NSDF_ERR_MISALIGNED;
+  if (!nsdf::device_memory(verts) || !nsdf::device_memory(faces) || !nsdf::device_memory(pts) ||
+      !nsdf::device_memory(out_sdf))
+    return NSDF_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   return nsdf::launch_mesh_sdf(verts, n_verts, faces, n_faces, reinterpret_cast<const float4 *>(pts),
                                n, out_sdf, 0, nullptr, nullptr, s) == cudaSuccess

@@ -51,18 +51,6 @@ size_t usable_bytes() {
   return lim != 0 && lim < kNoAllocScratchBytes ? lim : kNoAllocScratchBytes;
 }
 
-// True for memory the GPU addresses as device memory (device or managed).
-// cudaPointerGetAttributes allocates nothing.  A host array handed to this
-// entry point is rejected here instead of reaching a kernel.
-bool is_device_ptr(const void *p) {
-  cudaPointerAttributes attr;
-  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
-}
-
 // Device address of g_noalloc_scratch on the current device (host code only
 // sees a host-side stand-in for the symbol).  Resolved once per device and
 // kept for the life of the process: a device reset (cudaDeviceReset) would
@@ -97,8 +85,8 @@ extern "C" nsdf_status nsdf_collide_noalloc(nsdf_ctx *ctx, const float *pts, int
   if (!pts || !out_pts) return NSDF_ERR_INVALID_ARG;
   auto mis = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
   if (mis(pts) || mis(out_pts) || (out_n_sdf && mis(out_n_sdf))) return NSDF_ERR_MISALIGNED;
-  if (!is_device_ptr(pts) || !is_device_ptr(out_pts) || (out_n_sdf && !is_device_ptr(out_n_sdf)) ||
-      (out_hit && !is_device_ptr(out_hit)))
+  if (!device_memory(pts) || !device_memory(out_pts) || (out_n_sdf && !device_memory(out_n_sdf)) ||
+      (out_hit && !device_memory(out_hit)))
     return NSDF_ERR_INVALID_ARG;
   QueryParams p{};
   int num_sms = 0, width = 0, n_hidden = 0;

@@ -106,6 +106,14 @@ struct QueryParams {
 // Floats per network in QueryParams::g_T.
 constexpr int kBodyFloats = 24;
 
+// True for memory the GPU addresses as device memory (device or managed
+// allocations).  Every entry point that takes DEVICE pointers rejects
+// anything else with NSDF_ERR_INVALID_ARG before it launches, so that a host
+// array passed by mistake never reaches a kernel.  cudaPointerGetAttributes
+// allocates nothing and does not synchronise, so the check also runs while
+// a stream is being captured into a CUDA graph.
+bool device_memory(const void *p);
+
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_query_fp32(const QueryParams &p, int num_sms, cudaStream_t s);
 size_t query_fp32_scratch_bytes(int width, int n_hidden, int grid);

@@ -303,6 +303,9 @@ extern "C" nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n, 
   if ((reinterpret_cast<uintptr_t>(pts) & 15u) || (reinterpret_cast<uintptr_t>(g_weights) & 3u) ||
       (reinterpret_cast<uintptr_t>(targets) & 3u))
     return NSDF_ERR_MISALIGNED;
+  if (!device_memory(pts) || !device_memory(targets) || !device_memory(g_weights) ||
+      (loss && !device_memory(loss)))
+    return NSDF_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void **slot = ctx_train_slot(ctx);
   if (!*slot) *slot = new (std::nothrow) TrainState;

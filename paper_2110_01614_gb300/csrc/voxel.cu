@@ -109,15 +109,6 @@ bool make_box(int n, const float *lo, const float *hi, Box *b) {
   return true;
 }
 
-bool is_device(const void *p) {
-  cudaPointerAttributes attr;
-  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 }  // namespace nsdf
 
@@ -129,7 +120,7 @@ extern "C" nsdf_status nsdf_voxel_build(const float *verts, int64_t n_verts, con
   Box b{};
   if (!make_box(n, lo, hi, &b) || !verts || !faces || !grid || n_faces <= 0 || n_verts < 3)
     return NSDF_ERR_INVALID_ARG;
-  if (!is_device(verts) || !is_device(faces) || !is_device(grid)) return NSDF_ERR_INVALID_ARG;
+  if (!device_memory(verts) || !device_memory(faces) || !device_memory(grid)) return NSDF_ERR_INVALID_ARG;
   const int64_t nodes = (int64_t)n * n * n;
   return launch_mesh_sdf(verts, n_verts, faces, n_faces, nullptr, nodes, grid, n, b.lo, b.h,
                          reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
@@ -146,8 +137,8 @@ extern "C" nsdf_status nsdf_voxel_collide(const float *grid, int n, const float 
   if (!grid || !pts || !out_pts) return NSDF_ERR_INVALID_ARG;
   auto mis = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
   if (mis(pts) || mis(out_pts) || (out_n_sdf && mis(out_n_sdf))) return NSDF_ERR_MISALIGNED;
-  if (!is_device(grid) || !is_device(pts) || !is_device(out_pts) ||
-      (out_n_sdf && !is_device(out_n_sdf)) || (out_hit && !is_device(out_hit)))
+  if (!device_memory(grid) || !device_memory(pts) || !device_memory(out_pts) ||
+      (out_n_sdf && !device_memory(out_n_sdf)) || (out_hit && !device_memory(out_hit)))
     return NSDF_ERR_INVALID_ARG;
   const int64_t blocks = (n_pts + 255) / 256;
   voxel_collide_kernel<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
