@@ -339,6 +339,7 @@ nsdf_status nsdf_mesh_sdf(const float *verts, int64_t n_verts,
  * shear springs with rest lengths from the grid spacings hx (along rows) and
  * hz (between rows), unit mass, Hooke constant k_over_m, gravity (0, -g, 0):
  *   x_new = 2 x - x_prev + dt^2 a(x).
+ * nx <= 2^30, ny <= 65535.
  * Writes x_new into x_prev's buffer (the caller swaps the two).  x and
  * x_prev_inout are DEVICE memory (host memory: NSDF_ERR_INVALID_ARG).  The
  * collision solve is a separate nsdf_collide call on the result.

@@ -58,7 +58,8 @@ extern "C" nsdf_status nsdf_cloth_step(const float *x, float *x_prev_inout, int 
                                        nsdf_stream stream) {
   if (nx < 0 || ny < 0 || !(hx > 0.f) || !(hz > 0.f) || !(dt > 0.f)) return NSDF_ERR_INVALID_ARG;
   if (nx == 0 || ny == 0) return NSDF_OK;
-  if (!x || !x_prev_inout || x == x_prev_inout || ny > 65535) return NSDF_ERR_INVALID_ARG;
+  if (!x || !x_prev_inout || x == x_prev_inout || ny > 65535 || nx > (1 << 30))
+    return NSDF_ERR_INVALID_ARG;   // grid.y limit; the column index stays an int
   if ((reinterpret_cast<uintptr_t>(x) & 15u) || (reinterpret_cast<uintptr_t>(x_prev_inout) & 15u))
     return NSDF_ERR_MISALIGNED;
   if (!nsdf::device_memory(x) || !nsdf::device_memory(x_prev_inout)) return NSDF_ERR_INVALID_ARG;

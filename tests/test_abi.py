@@ -76,3 +76,13 @@ def test_null_context_calls_fail_cleanly(nsdf_lib):
     assert nsdf_lib.nsdf_mesh_sdf(None, 0, None, 0, None, -1, None, None) == 1
     assert nsdf_lib.nsdf_mesh_sdf(None, 0, None, 0, None, 0, None, None) == 0
     assert nsdf_lib.nsdf_cloth_step(None, None, 0, 4, 0.1, 0.1, 1.0, 9.81, 1e-3, None) == 0
+
+
+def test_cloth_step_rejects_sizes_beyond_its_index_range(nsdf_lib):
+    """Rows beyond the grid's y limit and columns beyond 2^30 are refused
+    before any pointer is examined (the addresses here are never touched)."""
+    fake_a, fake_b = 1 << 20, 2 << 20
+    assert nsdf_lib.nsdf_cloth_step(fake_a, fake_b, 64, 65536, 0.1, 0.1, 1.0, 9.81, 1e-3, None) == 1
+    assert nsdf_lib.nsdf_cloth_step(fake_a, fake_b, (1 << 30) + 1, 2, 0.1, 0.1, 1.0, 9.81, 1e-3,
+                                    None) == 1
+    assert nsdf_lib.nsdf_cloth_step(fake_a, fake_a, 64, 2, 0.1, 0.1, 1.0, 9.81, 1e-3, None) == 1
