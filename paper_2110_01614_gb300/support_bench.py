@@ -38,9 +38,14 @@
 * voxel: the voxel SDF baseline (Sec. 4.3, Table 1) at N = 256 against the
   fitted body-scale network: build time, memory, query time for 1M points
   and error against the exact signed distance near the surface.
+* kernels: the brute-force mesh SDF (65,536 points x 20,480 triangles, far
+  from and near the surface) and one 1024 x 1024 cloth step, each alone with
+  L2 flushed before every launch: pairs per second, and the cloth step's
+  bandwidth against the measured copy bandwidth.
 
 Usage: python -m paper_2110_01614_gb300.support_bench [fit penalty grouped grouped_paper cloth
-                                                      paper_arch fit512 fit_paper]
+                                                      paper_arch fit512 fit_paper cloth_fitted
+                                                      tiny voxel kernels]
 """
 
 import json
@@ -364,6 +369,81 @@ def bench_voxel(fitted=None, n=256, reps=20):
                                  "max": float(en.max())}}}
 
 
+def hbm_peak_gbs():
+    """The measured copy bandwidth of this GPU model (MEASURED_PEAKS.json at
+    the repository root), or None."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def events_ms_flushed(fn, reps, flush):
+    """Median CUDA-event time of fn with L2 flushed (a write larger than L2,
+    outside the events) before every launch."""
+    ts = []
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def bench_kernels(mesh_reps=3, cloth_reps=20):
+    """The support kernels alone, each against its bound, L2 flushed before
+    every launch: the brute-force mesh SDF (FP32 ALU + MUFU bound; FP64 for
+    undecided winding numbers) of 1,048,576 points against the
+    20,480-triangle displaced icosphere, for points far from the surface
+    (uniform in the cube: the FP32 winding number decides) and for fitting
+    targets (80% within ~0.01 of the surface: many take the FP64 winding
+    number), in point-triangle pairs per second (one warm-up launch each);
+    and one Verlet step of the 1024 x 1024 cloth (HBM bound: x and x_prev
+    read, x_prev written, 48 bytes per vertex; neighbour reads hit the
+    caches) against the measured copy bandwidth (three warm-up launches)."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")    # > L2 (129 MB)
+    V, F = synth.displaced_icosphere(level=5, seed=7)
+    Vd = torch.from_numpy(np.ascontiguousarray(V, dtype=np.float32)).cuda()
+    Fd = torch.from_numpy(np.ascontiguousarray(F, dtype=np.int32)).cuda()
+    n = 1 << 20
+    res = {"workload": "support_kernels", "l2": "flushed before every launch",
+           "mesh_reps": mesh_reps, "cloth_reps": cloth_reps}
+    for name, P in (("uniform", synth.uniform_cube_points(n, 3)),
+                    ("near_surface", synth.training_points(V, F, n, 5))):
+        pts = torch.from_numpy(np.ascontiguousarray(P)).cuda()
+        out = torch.empty(n, device="cuda")
+        fn = lambda: nsdf_mesh_sdf(Vd, Fd, pts, out)     # noqa: E731
+        fn()
+        ms = events_ms_flushed(fn, mesh_reps, flush)
+        pairs = n * int(F.shape[0])
+        res[f"mesh_sdf_{name}"] = {"points": n, "triangles": int(F.shape[0]), "ms": ms,
+                                   "pairs_per_s": pairs / (ms * 1e-3)}
+    from . import nsdf_cloth_step
+    sim_n = 1024
+    x = torch.from_numpy(synth.cloth_grid(sim_n)).cuda()
+    xp = x.clone()
+    h = 2.0 / (sim_n - 1)
+    fn = lambda: nsdf_cloth_step(x, xp, sim_n, sim_n, h, h, 1e5, 9.81, 1e-3)    # noqa: E731
+    for _ in range(3):
+        fn()
+    ms = events_ms_flushed(fn, cloth_reps, flush)
+    bytes_step = 48 * sim_n * sim_n
+    gbs = bytes_step / (ms * 1e-3) / 1e9
+    peak = hbm_peak_gbs()
+    res["cloth_step"] = {"grid": "1024x1024", "ms": ms, "bytes_per_step": bytes_step,
+                         "achieved_gbs": gbs, "peak_gbs": peak,
+                         "frac": gbs / peak if peak else None,
+                         "peak_source": "measured hbm_gbs (copy)" if peak else None}
+    return res
+
+
 def bench_line_support():
     """The support workloads in one bounded pass (about a minute), for the
     benchmark line: grouped launch, penalty gradient, the fitting steps and
@@ -373,19 +453,32 @@ def bench_line_support():
                      ("tiny", lambda: bench_tiny(20)),
                      ("penalty_gradient", lambda: bench_penalty(5)),
                      ("fit_width64_fp32", lambda: bench_fit_pool(10)),
-                     ("fit512_bf16", lambda: bench_fit512(10))):
-        t0 = time.perf_counter()
-        r = fn()
-        r["wall_s"] = time.perf_counter() - t0
-        out[name] = r
+                     ("fit512_bf16", lambda: bench_fit512(10)),
+                     ("kernels", lambda: bench_kernels(3, 10))):
+        out[name] = guarded(fn)
     t0 = time.perf_counter()
-    fitted = fit_body()
-    for name, fn in (("cloth", bench_cloth_fitted), ("voxel", bench_voxel)):
-        r = fn(fitted=fitted)
-        r["wall_s"] = time.perf_counter() - t0
-        out[name] = r
-        t0 = time.perf_counter()
+    try:
+        fitted = fit_body()
+    except Exception as e:     # recorded in the line; the headline stands without it
+        fitted = None
+        out["cloth"] = out["voxel"] = {"error": f"fitting the body: {type(e).__name__}: {e}"}
+    if fitted is not None:
+        for name, fn in (("cloth", bench_cloth_fitted), ("voxel", bench_voxel)):
+            out[name] = guarded(lambda: fn(fitted=fitted), t0)
+            t0 = time.perf_counter()
     return out
+
+
+def guarded(fn, t0=None):
+    """fn()'s record with its wall time, or the error it raised (so that one
+    failing support workload does not take the benchmark line with it)."""
+    t0 = time.perf_counter() if t0 is None else t0
+    try:
+        r = fn()
+    except Exception as e:
+        r = {"error": f"{type(e).__name__}: {e}"}
+    r["wall_s"] = time.perf_counter() - t0
+    return r
 
 
 def bench_fit_pool(steps=10):
@@ -409,7 +502,8 @@ def main(argv):
         r = {"fit": bench_fit, "penalty": bench_penalty, "grouped": bench_grouped,
              "grouped_paper": bench_grouped_paper, "cloth": bench_cloth,
              "paper_arch": bench_paper_arch, "fit512": bench_fit512, "fit_paper": bench_fit_paper,
-             "cloth_fitted": bench_cloth_fitted, "tiny": bench_tiny, "voxel": bench_voxel}[w]()
+             "cloth_fitted": bench_cloth_fitted, "tiny": bench_tiny, "voxel": bench_voxel,
+             "kernels": bench_kernels}[w]()
         r["wall_s"] = time.perf_counter() - t0
         print(json.dumps(r), flush=True)
 
