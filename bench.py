@@ -42,13 +42,15 @@ MAC_PER_QUERY = 3_670_528
 FLOP_PER_QUERY = 2 * MAC_PER_QUERY
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the tensor-core kernel on this workload, from one ncu capture, keyed by the
-# SHA-256 of the kernel's code (query_tc16.cu and its headers tc_ptx.cuh,
-# softplus.cuh and f32x2.cuh, comments and blank lines removed) it was taken
-# on; reported only while that code is unchanged.
+# the tensor-core kernel on this workload, and the share of active cycles its
+# tensor pipe was busy (sm__pipe_tensor_cycles_active), from ncu captures
+# keyed by the SHA-256 of the kernel's code (query_tc16.cu and its headers
+# tc_ptx.cuh, softplus.cuh and f32x2.cuh, comments and blank lines removed)
+# they were taken on; reported only while that code is unchanged.
 TRAFFIC_CAPTURE = {
     "code_sha256": "0a3c6783a47c08d56a359cb56463f7bfbf7537df188fa8f25ad0c25e3a118f52",
     "bytes_per_launch": 4.003539e9 + 4.895270e9,
+    "tensor_pipe_active_pct": 44.9,
 }
 
 
@@ -75,12 +77,17 @@ def kernel_code_sha256():
     return code_sha256("\n".join(text))
 
 
-def traffic_bytes():
+def captured(key):
+    """A figure of the ncu captures, while the kernel's code is the captured code."""
     try:
         h = kernel_code_sha256()
     except OSError:
         return None
-    return TRAFFIC_CAPTURE["bytes_per_launch"] if h == TRAFFIC_CAPTURE["code_sha256"] else None
+    return TRAFFIC_CAPTURE[key] if h == TRAFFIC_CAPTURE["code_sha256"] else None
+
+
+def traffic_bytes():
+    return captured("bytes_per_launch")
 
 
 def load_peaks():
@@ -421,6 +428,8 @@ def run_gpu(args):
                      "peak_source": f"{peak_kind} bf16_tflops (burst, cuBLAS)",
                      "traffic": traffic_bytes() if n == N_POINTS else None,
                      "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                     "tensor_pipe_active_pct": (captured("tensor_pipe_active_pct")
+                                                if n == N_POINTS else None),
                      "kernel": "query_tc16_kernel<bf16>",
                      "algorithmic_flop_per_launch": FLOP_PER_QUERY * n,
                      "algorithmic_io_bytes_per_launch": 49 * n},

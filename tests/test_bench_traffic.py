@@ -24,8 +24,19 @@ def test_traffic_reported_only_for_the_captured_code(monkeypatch):
     current = bench.kernel_code_sha256()
     monkeypatch.setitem(bench.TRAFFIC_CAPTURE, "code_sha256", current)
     assert bench.traffic_bytes() == bench.TRAFFIC_CAPTURE["bytes_per_launch"]
+    assert bench.captured("tensor_pipe_active_pct") == bench.TRAFFIC_CAPTURE["tensor_pipe_active_pct"]
     monkeypatch.setitem(bench.TRAFFIC_CAPTURE, "code_sha256", "0" * 64)
     assert bench.traffic_bytes() is None
+    assert bench.captured("tensor_pipe_active_pct") is None
+
+
+def test_committed_tensor_pipe_share_matches_the_profile_summary():
+    """The figure in the bench line is the one the committed ncu summary of the
+    same code reports."""
+    text = open(os.path.join(ROOT, "profiles", "query_tc16_body_scale_1M.txt")).read()
+    assert bench.TRAFFIC_CAPTURE["code_sha256"] in text
+    line = [l for l in text.splitlines() if l.strip().startswith("tensor pipe active")][0]
+    assert float(line.split()[-2]) == bench.TRAFFIC_CAPTURE["tensor_pipe_active_pct"]
 
 
 def test_committed_capture_is_plausible_for_the_workload():
