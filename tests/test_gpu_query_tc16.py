@@ -193,3 +193,39 @@ def test_one_cta_form_matches_pairs_and_oracle(nsdf, prec, blob, n):
         np.testing.assert_array_equal(a, b)
     f, N, hit, x = mlp.collide(blob, BODY, pts, EPS)
     check(prec, f, N, hit, x, *one, pts)
+
+
+def test_empty_input_launches_nothing(nsdf, prec, blob):
+    """n = 0 returns at once: nothing is written and no error is recorded."""
+    s = nsdf.NeuralSDF(BODY, P(nsdf, prec)).load(blob)
+    lib = nsdf.library()
+    buf = torch.full((4, 4), 7.0, device="cuda")
+    assert lib.nsdf_collide(s.ctx, buf.data_ptr(), 0, EPS, None, buf.data_ptr(), None, None,
+                            None) == 0
+    assert lib.nsdf_query(s.ctx, buf.data_ptr(), 0, buf.data_ptr(), 0, None) == 0
+    nsdf.nsdf_sync_status(s.ctx)
+    torch.cuda.synchronize()
+    assert bool((buf == 7.0).all())
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def big_points():
+    return synth.body_scale_points((1 << 24) + 77, 21)
+
+
+def test_sixteen_million_points_sampled_parity(nsdf, prec, blob, big_points):
+    """2^24 + 77 points (16 times the benchmark's launch; the last tile holds
+    77 points) in one call: 4,096 seeded points and the last 300 against the
+    oracle, and at every point finite outputs, unit normals and hit <=> f < eps."""
+    pts = big_points
+    n = pts.shape[0]
+    out_pts, out_ns, out_hit = collide_gpu(nsdf, prec, blob, pts)
+    u = (synth.Stream(7).u64(4096) % np.uint64(n)).astype(np.int64)
+    idx = np.unique(np.concatenate([u, np.arange(n - 300, n)]))
+    f, N, hit, x = mlp.collide(blob, BODY, pts[idx], EPS)
+    check(prec, f, N, hit, x, out_pts[idx], out_ns[idx], out_hit[idx], pts[idx])
+    assert np.isfinite(out_ns).all() and np.isfinite(out_pts).all()
+    nrm = np.linalg.norm(out_ns[:, :3], axis=1)
+    assert np.all(np.abs(nrm - 1.0) < 1e-5)
+    np.testing.assert_array_equal(out_hit, out_ns[:, 3] < EPS)
