@@ -61,6 +61,54 @@ def _ptr(t):
     return int(t)
 
 
+# Argument checks of the binding: the C ABI sees bare pointers and counts, so
+# a tensor of the wrong dtype or size would make a kernel read or write past
+# its end.  These refuse such tensors (ValueError) before the library is
+# called; raw integer pointers pass unchecked.
+def _records(t, name, rows=None, optional=False):
+    """float4 records: a float32 [n, 4] tensor with at least `rows` rows."""
+    if t is None and optional or not isinstance(t, torch.Tensor):
+        return
+    if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 4:
+        raise ValueError(f"{name} must be a float32 [n, 4] tensor of float4 records, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+    if rows is not None and t.shape[0] < rows:
+        raise ValueError(f"{name} holds {t.shape[0]} records; the call needs {rows}")
+
+
+def _values(t, name, dtypes, count, optional=False):
+    """A tensor of one of `dtypes` with at least `count` elements."""
+    if t is None and optional or not isinstance(t, torch.Tensor):
+        return
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name} must be {' or '.join(str(d) for d in dtypes)}, got {t.dtype}")
+    if t.numel() < count:
+        raise ValueError(f"{name} holds {t.numel()} values; the call needs {count}")
+
+
+def _triangles(verts, faces):
+    _values(verts, "verts", (torch.float32,), 0)
+    _values(faces, "faces", (torch.int32,), 0)
+    for t, name in ((verts, "verts"), (faces, "faces")):
+        if isinstance(t, torch.Tensor) and (t.dim() != 2 or t.shape[1] != 3):
+            raise ValueError(f"{name} must be [n, 3], got {tuple(t.shape)}")
+
+
+def _work_list(pts, offsets, counts, max_total, out_pts, out_n_sdf, T=None):
+    _records(pts, "pts", max_total)
+    _records(out_pts, "out_pts", max_total)
+    _records(out_n_sdf, "out_n_sdf", max_total, optional=True)
+    _values(offsets, "offsets", (torch.int64,), 0)
+    _values(counts, "counts", (torch.int64,), 0)
+    if isinstance(offsets, torch.Tensor) and isinstance(counts, torch.Tensor):
+        if offsets.numel() != counts.numel():
+            raise ValueError("offsets and counts must have one entry per network")
+        _values(T, "T", (torch.float32,), 16 * offsets.numel(), optional=True)
+
+
+_HIT = (torch.uint8, torch.bool)
+
+
 def _stream(stream):
     if stream is None:
         return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
@@ -109,6 +157,8 @@ def nsdf_load_weights(ctx, net, w, stream=None):
 
 
 def nsdf_query(ctx, pts, out_n_sdf, flags=0, stream=None):
+    _records(pts, "pts")
+    _records(out_n_sdf, "out_n_sdf", pts.shape[0])
     _check(library().nsdf_query(ctx, _ptr(pts), pts.shape[0], _ptr(out_n_sdf), int(flags),
                                 _stream(stream)), "nsdf_query")
 
@@ -120,7 +170,16 @@ def _transform(T):
     return (ctypes.c_float * 16)(*a.tolist())
 
 
+def _collide_args(pts, out_pts, out_n_sdf, out_hit):
+    _records(pts, "pts")
+    n = pts.shape[0]
+    _records(out_pts, "out_pts", n)
+    _records(out_n_sdf, "out_n_sdf", n, optional=True)
+    _values(out_hit, "out_hit", _HIT, n, optional=True)
+
+
 def nsdf_collide(ctx, pts, eps, out_pts, out_n_sdf=None, out_hit=None, T=None, stream=None):
+    _collide_args(pts, out_pts, out_n_sdf, out_hit)
     Tc = _transform(T)
     _check(library().nsdf_collide(ctx, _ptr(pts), pts.shape[0], float(eps),
                                   ctypes.cast(Tc, ctypes.c_void_p) if Tc is not None else None,
@@ -137,6 +196,7 @@ def nsdf_collide_noalloc(ctx, pts, eps, out_pts, out_n_sdf=None, out_hit=None, T
                     ("out_hit", out_hit)):
         if t is not None and not getattr(t, "is_cuda", False):
             raise ValueError(f"nsdf_collide_noalloc: {name} must be a CUDA tensor")
+    _collide_args(pts, out_pts, out_n_sdf, out_hit)
     Tc = _transform(T)
     _check(library().nsdf_collide_noalloc(ctx, _ptr(pts), pts.shape[0], float(eps),
                                           ctypes.cast(Tc, ctypes.c_void_p) if Tc is not None
@@ -146,6 +206,12 @@ def nsdf_collide_noalloc(ctx, pts, eps, out_pts, out_n_sdf=None, out_hit=None, T
 
 
 def nsdf_backward(ctx, pts, g_sdf, g_grad=None, g_weights=None, g_pts=None, stream=None):
+    _records(pts, "pts")
+    n = pts.shape[0]
+    _values(g_sdf, "g_sdf", (torch.float32,), n)
+    _records(g_grad, "g_grad", n, optional=True)
+    _values(g_weights, "g_weights", (torch.float32,), 0, optional=True)
+    _records(g_pts, "g_pts", n, optional=True)
     _check(library().nsdf_backward(ctx, _ptr(pts), pts.shape[0], _ptr(g_sdf), _ptr(g_grad),
                                    _ptr(g_weights), _ptr(g_pts), _stream(stream)),
            "nsdf_backward")
@@ -153,6 +219,7 @@ def nsdf_backward(ctx, pts, g_sdf, g_grad=None, g_weights=None, g_pts=None, stre
 
 def nsdf_query_grouped(ctx, pts, offsets, counts, max_total, eps, out_pts, out_n_sdf=None,
                        stream=None):
+    _work_list(pts, offsets, counts, max_total, out_pts, out_n_sdf)
     _check(library().nsdf_query_grouped(ctx, _ptr(pts), _ptr(offsets), _ptr(counts),
                                         int(max_total), float(eps), _ptr(out_pts),
                                         _ptr(out_n_sdf), _stream(stream)), "nsdf_query_grouped")
@@ -161,6 +228,7 @@ def nsdf_query_grouped(ctx, pts, offsets, counts, max_total, eps, out_pts, out_n
 def nsdf_query_grouped_T(ctx, pts, offsets, counts, max_total, eps, T, out_pts, out_n_sdf=None,
                          stream=None):
     """nsdf_query_grouped with a device [n_nets, 4, 4] tensor of body poses."""
+    _work_list(pts, offsets, counts, max_total, out_pts, out_n_sdf, T)
     _check(library().nsdf_query_grouped_T(ctx, _ptr(pts), _ptr(offsets), _ptr(counts),
                                           int(max_total), float(eps), _ptr(T), _ptr(out_pts),
                                           _ptr(out_n_sdf), _stream(stream)), "nsdf_query_grouped_T")
@@ -168,6 +236,10 @@ def nsdf_query_grouped_T(ctx, pts, offsets, counts, max_total, eps, T, out_pts, 
 
 def nsdf_l1_grad(ctx, pts, targets, g_weights, loss=None, stream=None):
     """Gradient of mean |f(p) - d| for a 16-bit context (Sec. 3.1 fitting loss)."""
+    _records(pts, "pts")
+    _values(targets, "targets", (torch.float32,), pts.shape[0])
+    _values(g_weights, "g_weights", (torch.float32,), 0)
+    _values(loss, "loss", (torch.float32,), 1, optional=True)
     _check(library().nsdf_l1_grad(ctx, _ptr(pts), pts.shape[0], _ptr(targets), _ptr(g_weights),
                                   _ptr(loss), _stream(stream)), "nsdf_l1_grad")
 
@@ -175,6 +247,7 @@ def nsdf_l1_grad(ctx, pts, targets, g_weights, loss=None, stream=None):
 def nsdf_autotune_grouped(ctx, pts, offsets, counts, max_total, eps, out_pts, out_n_sdf=None,
                           stream=None):
     """Time the grouped launch's tile shapes on this problem; returns (points/thread, CTAs/SM)."""
+    _work_list(pts, offsets, counts, max_total, out_pts, out_n_sdf)
     chosen = (ctypes.c_int * 2)()
     _check(library().nsdf_autotune_grouped(ctx, _ptr(pts), _ptr(offsets), _ptr(counts),
                                            int(max_total), float(eps), _ptr(out_pts),
@@ -189,12 +262,17 @@ def nsdf_set_grouped_config(ctx, points_per_thread, ctas_per_sm):
 
 
 def nsdf_mesh_sdf(verts, faces, pts, out_sdf, stream=None):
+    _triangles(verts, faces)
+    _records(pts, "pts")
+    _values(out_sdf, "out_sdf", (torch.float32,), pts.shape[0])
     _check(library().nsdf_mesh_sdf(_ptr(verts), verts.shape[0], _ptr(faces), faces.shape[0],
                                    _ptr(pts), pts.shape[0], _ptr(out_sdf), _stream(stream)),
            "nsdf_mesh_sdf")
 
 
 def nsdf_cloth_step(x, x_prev, nx, ny, hx, hz, k_over_m, g, dt, stream=None):
+    _records(x, "x", int(nx) * int(ny))
+    _records(x_prev, "x_prev", int(nx) * int(ny))
     _check(library().nsdf_cloth_step(_ptr(x), _ptr(x_prev), int(nx), int(ny), float(hx),
                                      float(hz), float(k_over_m), float(g), float(dt),
                                      _stream(stream)), "nsdf_cloth_step")
@@ -224,6 +302,8 @@ def _box(lo, hi):
 
 def nsdf_voxel_build(verts, faces, n, lo, hi, grid, stream=None):
     """Fill grid (device float [n^3]) with the exact signed distance of every node."""
+    _triangles(verts, faces)
+    _values(grid, "grid", (torch.float32,), int(n) ** 3 if int(n) > 0 else 0)
     a, b = _box(lo, hi)
     _check(library().nsdf_voxel_build(_ptr(verts), verts.shape[0], _ptr(faces), faces.shape[0],
                                       int(n), ctypes.cast(a, ctypes.c_void_p),
@@ -234,6 +314,8 @@ def nsdf_voxel_build(verts, faces, n, lo, hi, grid, stream=None):
 def nsdf_voxel_collide(grid, n, lo, hi, pts, eps, out_pts, out_n_sdf=None, out_hit=None,
                        stream=None):
     """The collision query answered from a voxel grid (trilinear interpolation)."""
+    _values(grid, "grid", (torch.float32,), int(n) ** 3 if int(n) > 0 else 0)
+    _collide_args(pts, out_pts, out_n_sdf, out_hit)
     a, b = _box(lo, hi)
     _check(library().nsdf_voxel_collide(_ptr(grid), int(n), ctypes.cast(a, ctypes.c_void_p),
                                         ctypes.cast(b, ctypes.c_void_p), _ptr(pts), pts.shape[0],
