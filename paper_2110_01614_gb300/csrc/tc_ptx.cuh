@@ -297,8 +297,8 @@ __device__ __forceinline__ uint32_t pack16(float lo, float hi) {
   }
 }
 
-// The driver's cuTensorMapEncodeTiled, looked up once through the runtime
-// (host code; null if the driver does not provide it).
+// cuTensorMapEncodeTiled of the CUDA driver API (libcuda), looked up once
+// through the runtime (host code; null if the installed libcuda lacks it).
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
