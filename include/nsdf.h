@@ -227,8 +227,9 @@ nsdf_status nsdf_l1_grad(nsdf_ctx *ctx, const float *pts, int64_t n,
  * with the collision solve of nsdf_collide (no transform).  offsets and
  * counts are DEVICE int64 arrays: the work list is built on the device, so a
  * CUDA graph that captured this call replays correctly with new counts.
- * max_total bounds offsets[k] + counts[k] (a violating entry is skipped and
- * reported by nsdf_sync_status as NSDF_ERR_INVALID_ARG) and sizes the launch.
+ * max_total (at most 2^34) bounds offsets[k] + counts[k] (a violating entry
+ * is skipped and reported by nsdf_sync_status as NSDF_ERR_INVALID_ARG) and
+ * sizes the launch.
  * out_n_sdf nullable; points outside every range are left untouched.  pts,
  * out_pts and out_n_sdf are DEVICE memory too (a host array, or host
  * offsets / counts: NSDF_ERR_INVALID_ARG, nothing is launched).

@@ -754,8 +754,14 @@ struct GroupedArgs {
   const float *T = nullptr;   // device [n_nets][16] poses, or none
 };
 
+// Above 2^34 points (275 GB of float4 records, more than the GPU holds) the
+// device-built tile list could pass 2^31 tiles of the smallest (16-point)
+// tile shape and overflow its int32 starts.
+constexpr int64_t kMaxGroupedPoints = int64_t(1) << 34;
+
 nsdf_status grouped_check(nsdf_ctx *ctx, const GroupedArgs &g) {
-  if (!ctx || g.max_total < 0 || !std::isfinite(g.eps)) return NSDF_ERR_INVALID_ARG;
+  if (!ctx || g.max_total < 0 || g.max_total > kMaxGroupedPoints || !std::isfinite(g.eps))
+    return NSDF_ERR_INVALID_ARG;
   if (g.max_total == 0) return NSDF_OK;
   if (!g.pts || !g.offsets || !g.counts || !g.out_pts) return NSDF_ERR_INVALID_ARG;
   if (!aligned16(g.pts) || !aligned16(g.out_pts) || (g.out_n_sdf && !aligned16(g.out_n_sdf)))
